@@ -1,0 +1,324 @@
+"""Benchmark: 2048-bit constant-time modexp/s (and Montmul/s) on GB300.
+
+One step = one modexp_consttime call over the whole batch (65536 instances of
+2048-bit moduli, half random odd and half products of two 1024-bit primes;
+uniform bases; full-length 2048-bit exponents; window 5; truncated Montgomery;
+interleaved layout): to-Montgomery conversion, window table, 410 windows of 5
+squarings + a masked table scan + a product, and the conversion back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs its own batch
+(weak scaling, no collective on the data path); `value` = all instances of all
+ranks / the slowest rank's time. `--impl reference` times the CPU oracle (plain
+left-to-right square-and-multiply) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2048-bit const-time modexp/s and Montmul/s on 1 GB300; p99 latency under load"
+BITS, WINDOW = 2048, 5
+
+
+def imad_counts(n: int):
+    """Algorithmic 32-bit multiply-add count (each partial product = a lo and a hi
+    multiply-add) of one Montgomery product / square, truncated (Alg. 6) and full (Alg. 5)."""
+    return {
+        "mul_trunc": 4 * n * n + 2 * n - 1,
+        "sqr_trunc": 3 * n * n + 3 * n - 1,
+        "mul_full": 5 * n * n,
+        "sqr_full": 4 * n * n + n,
+    }
+
+
+def modexp_imad(bits: int, ebits: int, w: int, red: str = "trunc") -> int:
+    n = (bits + 31) // 32
+    c = imad_counts(n)
+    windows = (ebits + w - 1) // w
+    sqrs = windows * w
+    muls = windows + 1 + ((1 << w) - 2) + 1     # windows, to-Montgomery, table, from-Montgomery
+    return sqrs * c["sqr_" + red] + muls * c["mul_" + red]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(b, ebits, budget_s: float, threads: int = 0):
+    """Time the CPU oracle's modexp on a sample of the workload sized for ~budget_s."""
+    import oracle
+    cores = oracle.threads_used(threads)
+    k = max(cores, 8)
+    t0 = time.perf_counter()
+    oracle.modexp(b.a[:k], b.e[:k], ebits, b.N[:k], threads)
+    dt = time.perf_counter() - t0
+    count = int(min(b.batch, max(k, k * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.modexp(b.a[:count], b.e[:count], ebits, b.N[:count], threads)
+    dt = time.perf_counter() - t0
+    return count / dt, cores, count, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+    import seeded_inputs as si
+
+    procs = min(16, os.cpu_count() or 1)
+    # inputs are generated before any CUDA call (the prime pool uses spawned workers)
+    b = si.batch_2048(seed=rank, batch=args.batch, procs=procs)
+    ebits = b.ebits
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps_rates = []
+        for s in range(args.warmup + args.steps):
+            rate, cores, count, dt = cpu_oracle_rate(b, ebits, budget_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+            if s >= args.warmup:
+                steps_rates.append((rate, cores, count, dt))
+        rate = statistics.median(r[0] for r in steps_rates)
+        cores, count = steps_rates[0][1], steps_rates[0][2]
+        line = {
+            "impl": "reference", "metric": METRIC, "value": rate, "unit": "modexp/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(r[3] for r in steps_rates),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batch_2048: 2048-bit moduli (half RSA-like), 2048-bit exponents, w=5",
+                       "batch": args.batch, "bits": BITS, "window": WINDOW},
+            "cpu_baseline": {"value": rate, "unit": "modexp/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{count} instances per step of the 65536-instance workload"},
+            "e2e": {"value": rate, "unit": "modexp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0,
+        }
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_2410_18129_gb300 as mp
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    IL = mp.LAYOUT_INTERLEAVED
+    B = args.batch
+    n = b.n
+    N = mp.to_device(mp.interleave(b.N))
+    A = mp.to_device(mp.interleave(b.a))
+    Bv = mp.to_device(mp.interleave(b.b))
+    E = mp.to_device(mp.interleave(b.e))
+    Y = torch.zeros_like(A)
+    ctx = mp.MontCtx(N, B, BITS, IL)
+    ws = torch.empty(mp.modexp_workspace_bytes(B, BITS, WINDOW) // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def step(red=mp.RED_TRUNCATED):
+        mp.modexp_consttime(Y, A, E, ebits, ctx, WINDOW, red, workspace=ws)
+
+    def timed(fn, k):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # roofline denominator: measured integer multiply-add rate per SM per clock
+    imad_rate, imad_mhz = mp.bench_imad(0, 2000)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+
+    for _ in range(args.warmup):
+        step()
+    # parity spot check of this run's output (sampled instances vs the oracle), outside timing
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed(step, args.steps)
+    clocks = clk.summary()
+    ms_step = ms / args.steps
+    value = world * B / (ms_step / 1e3)
+
+    # classical reduction for comparison
+    for _ in range(1):
+        step(mp.RED_FULL)
+    ms_full = timed(lambda: step(mp.RED_FULL), max(2, args.steps // 2)) / max(2, args.steps // 2)
+
+    # Montgomery products over the same batch
+    C = torch.zeros_like(A)
+    mm = {}
+    for red, nm in ((mp.RED_TRUNCATED, "trunc"), (mp.RED_FULL, "full")):
+        for _ in range(3):
+            mp.mont_mul(C, A, Bv, ctx, red)
+        k = 50
+        mm[nm] = world * B / (timed(lambda: mp.mont_mul(C, A, Bv, ctx, red), k) / k / 1e3)
+        for _ in range(3):
+            mp.mont_sqr(C, A, ctx, red)
+        mm[nm + "_sqr"] = world * B / (timed(lambda: mp.mont_sqr(C, A, ctx, red), k) / k / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D inputs, modexp, D2H result
+    hA = torch.from_numpy(mp.interleave(b.a).view(np.int32)).pin_memory()
+    hE = torch.from_numpy(mp.interleave(b.e).view(np.int32)).pin_memory()
+    hY = torch.empty(Y.numel(), dtype=torch.int32).pin_memory()
+    dA, dE = torch.empty_like(A), torch.empty_like(E)
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        dE.copy_(hE, non_blocking=True)
+        mp.modexp_consttime(Y, dA, dE, ebits, ctx, WINDOW, mp.RED_TRUNCATED, workspace=ws)
+        hY.copy_(Y, non_blocking=True)
+
+    e2e_step()
+    ms_e2e = timed(e2e_step, args.steps) / args.steps
+    h2d = (hA.numel() + hE.numel()) * 4
+    d2h = hY.numel() * 4
+
+    # sampled parity of the timed configuration (bit-exact vs the oracle)
+    parity = None
+    if rank == 0:
+        import oracle
+        idx = np.linspace(0, B - 1, 24).astype(int)
+        got = mp.deinterleave(mp.to_host(Y), B, n)[idx]
+        want = oracle.modexp(b.a[idx], b.e[idx], ebits, b.N[idx])
+        parity = {"sampled": int(idx.size), "mismatches": int((got != want).any(axis=1).sum())}
+
+    imad = modexp_imad(BITS, ebits, WINDOW, "trunc")
+    achieved = imad * B / (ms_step / 1e3) / 1e12
+    peak_clock = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak_clock = float(json.load(f).get("sm_max_mhz", peak_clock))
+    except Exception:
+        pass
+    peak = sms * imad_rate * peak_clock * 1e6 / 1e12
+    obs_clock = clocks["sm_mhz"] or imad_mhz
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_basis": f"{sms} SMs x {imad_rate:.1f} IMAD/clk/SM (measured) x {peak_clock:.0f} MHz max clock",
+                "frac_at_observed_clock": achieved / (sms * imad_rate * obs_clock * 1e6 / 1e12),
+                "imad_per_modexp": imad}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        rate, cores, count, dt = cpu_oracle_rate(b, ebits, args.cpu_budget)
+        cpu = {"value": rate, "unit": "modexp/s", "cores": cores, "kind": "oracle",
+               "sample": f"{count} of the 65536 instances ({dt:.1f} s), plain square-and-multiply"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "modexp/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batch_2048: 65536 x 2048-bit moduli (half random odd, half p*q of 1024-bit "
+                                   "primes), uniform bases, 2048-bit exponents, window 5, truncated Montgomery",
+                       "batch_per_gpu": B, "bits": BITS, "window": WINDOW, "layout": "interleaved",
+                       "l2": "working set (window tables 512 MiB + contexts) larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * B / (ms_e2e / 1e3), "unit": "modexp/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "modexp_full_reduction_per_s": world * B / (ms_full / 1e3),
+            "montmul_per_s": {"trunc": mm["trunc"], "full": mm["full"]},
+            "montsqr_per_s": {"trunc": mm["trunc_sqr"], "full": mm["full_sqr"]},
+            "parity": parity,
+            "imad_microbench": {"per_clk_per_sm": imad_rate, "implied_mhz": imad_mhz},
+        }
+        print(json.dumps(line))
+    ctx.free()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * mpgpu — batched multi-precision and Montgomery arithmetic on GB300 (sm_103a).
+ *
+ * C ABI of the library built from paper_2410_18129_gb300/csrc. Every entry point
+ * works on a batch of independent instances ("8 values in parallel" in the
+ * paper, Sec. 2; here any batch size). Values are little-endian arrays of
+ * 32-bit words, n = ceil(bits/32) words per value; bits above `bits` must be 0.
+ *
+ * Conventions shared by every call
+ *   - Data pointers are DEVICE pointers owned by the caller (e.g. torch tensors).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream and never synchronise it, except
+ *     mont_ctx_init / mont_ctx_free (documented there).
+ *   - Return value: MP_OK (0) or a negative mp_status. Argument errors are
+ *     detected on the host before any launch; launch failures map to MP_ERR_CUDA.
+ *   - Layout (mp_layout) of an array of `batch` values of w words each:
+ *       MP_LAYOUT_INSTANCE_MAJOR  word i of value k at  k*w + i            (GMP-like, Sec. 6.4)
+ *       MP_LAYOUT_INTERLEAVED     word i of value k at  ((i/4)*batch + k)*4 + i%4
+ *                                 (groups of four words of consecutive values side by side,
+ *                                 the GPU analogue of the word slicing of Table 1); such an
+ *                                 array holds ceil(w/4)*4*batch words.
+ *   - Montgomery radix R = 2^(32n). Montgomery-domain values are x*R mod N.
+ *     Every Montgomery output is canonical (< N): the library always performs the
+ *     final conditional subtraction that Alg. 5 leaves optional, because R = 2^(32n)
+ *     leaves no slack above a modulus whose top bit is set.
+ *   - Preconditions of mont_* and modexp: inputs < N, N odd with its top bit (bits-1) set.
+ *     Violations give unspecified (but memory-safe) results.
+ */
+#ifndef MPGPU_H
+#define MPGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MP_OK = 0,
+    MP_ERR_ARG = -1,            /* null pointer, zero batch, bad enum value */
+    MP_ERR_SIZE = -2,           /* bits == 0 or above mp_max_bits(), window out of range */
+    MP_ERR_EVEN_MODULUS = -3,   /* mont_ctx_init found an even modulus */
+    MP_ERR_ALIGN = -4,          /* pointer not 16-byte aligned */
+    MP_ERR_CUDA = -5,           /* a CUDA runtime call or kernel launch failed */
+    MP_ERR_NOMEM = -6,          /* device allocation failed or workspace too small */
+    MP_ERR_UNIMPLEMENTED = -7,  /* combination not provided by this build */
+    MP_ERR_TIMEOUT = -8         /* a bounded device-side wait gave up (persistent kernels) */
+} mp_status;
+
+typedef enum { MP_LAYOUT_INSTANCE_MAJOR = 0, MP_LAYOUT_INTERLEAVED = 1 } mp_layout;
+typedef enum { MP_ALGO_AUTO = 0, MP_ALGO_SCHOOLBOOK = 1, MP_ALGO_KARATSUBA = 2 } mp_algo;
+typedef enum { MP_RED_TRUNCATED = 0, MP_RED_FULL = 1 } mp_red;
+
+/* Opaque per-batch Montgomery context: device copies of N, N', R mod N, R^2 mod N. */
+typedef struct mont_ctx mont_ctx;
+
+/* Human-readable text for a status code (static storage). */
+const char *mp_strerror(int status);
+
+/* Largest operand size in bits supported by this build. */
+uint32_t mp_max_bits(void);
+
+/* Library version string (static storage). */
+const char *mp_version(void);
+
+/*
+ * Layout conversion (the expand / contract step of Sec. 6.4, Table 8; here a
+ * transpose, since the limb radix stays 2^32). dst and src hold `batch` values
+ * of `words` words; dst and src must not overlap.
+ */
+int mp_convert(uint32_t *dst, mp_layout dst_layout, const uint32_t *src, mp_layout src_layout,
+               size_t batch, uint32_t words, void *stream);
+
+/*
+ * Batch product C_k = A_k * B_k (Alg. 1 B_mul; Sec. 3 one-level Karatsuba).
+ * a, b: n words per instance; c: 2n words per instance; all in `layout`.
+ * algo: SCHOOLBOOK, KARATSUBA (one level; needs bits >= 1024) or AUTO
+ * (Karatsuba from 4096 bits up). c must not overlap a or b.
+ */
+int mp_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,
+           mp_layout layout, mp_algo algo, void *stream);
+
+/* Batch square C_k = A_k^2 (Alg. 2 B_square, Sec. 3). Same conventions as mp_mul. */
+int mp_sqr(uint32_t *c, const uint32_t *a, size_t batch, uint32_t bits, mp_layout layout,
+           mp_algo algo, void *stream);
+
+/*
+ * Build a Montgomery context for `batch` moduli N (n words each, `layout`):
+ * N' = (-N)^{-1} mod R, R mod N and R^2 mod N (Sec. 4: the precomputed values of
+ * Alg. 3 and the R^2 used to enter the Montgomery representation).
+ * Allocates device memory (owned by the context until mont_ctx_free) and
+ * synchronises `stream` to report moduli errors: if any N is even, returns
+ * MP_ERR_EVEN_MODULUS, stores the smallest offending instance index in
+ * *bad_index (when non-NULL) and creates no context. N is copied; the caller
+ * may free it afterwards. Operands of later calls use the same `layout`.
+ */
+int mont_ctx_init(mont_ctx **ctx, const uint32_t *N, size_t batch, uint32_t bits,
+                  mp_layout layout, size_t *bad_index, void *stream);
+
+/* Free a context (synchronises the device before freeing). NULL is accepted. */
+int mont_ctx_free(mont_ctx *ctx);
+
+/* Context properties: batch, bits, layout. Any out pointer may be NULL. */
+int mont_ctx_info(const mont_ctx *ctx, size_t *batch, uint32_t *bits, mp_layout *layout);
+
+/*
+ * Copy one context constant into a caller device buffer of n words per instance
+ * in the context layout: which = 0 N', 1 R mod N, 2 R^2 mod N, 3 N.
+ */
+int mont_ctx_export(const mont_ctx *ctx, int which, uint32_t *dst, void *stream);
+
+/*
+ * Batch Montgomery product c_k = a_k * b_k * R^{-1} mod N_k (Alg. 3 with B_mul,
+ * Alg. 5/6): red = MP_RED_TRUNCATED computes only the low half of q = T*N' mod R
+ * and only the high half of q*N (Alg. 6, Thm. 1, Thm. 2); MP_RED_FULL forms the
+ * whole T + q*N (Alg. 3, B_fma). Both give the same canonical result.
+ * a, b, c: n words per instance in the context layout; c may alias a or b.
+ */
+int mont_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, const mont_ctx *ctx, mp_red red,
+             mp_algo algo, void *stream);
+
+/* Batch Montgomery square c_k = a_k^2 * R^{-1} mod N_k (Alg. 2 then Alg. 5/6). */
+int mont_sqr(uint32_t *c, const uint32_t *a, const mont_ctx *ctx, mp_red red, mp_algo algo,
+             void *stream);
+
+/*
+ * Device workspace (bytes) that modexp_consttime needs for the window tables of
+ * `batch` instances of `bits` bits at window width `window` (1..6).
+ */
+size_t modexp_workspace_bytes(size_t batch, uint32_t bits, uint32_t window);
+
+/*
+ * Constant-time fixed-window left-to-right exponentiation y_k = base_k^{e_k} mod N_k
+ * (Alg. 7). exp holds ceil(exp_bits/32) words per instance (context layout);
+ * exp_bits is public and fixes the work: ceil(exp_bits/window) windows, each of
+ * `window` Montgomery squarings and one Montgomery product with a table entry
+ * chosen by a masked scan of the whole table (no secret-dependent branch or
+ * address). window = 0 picks the tuned width. base and y: n words per instance,
+ * ordinary residues (converted to and from the Montgomery domain inside).
+ * workspace: device buffer of at least modexp_workspace_bytes(...) bytes, 16-byte
+ * aligned; workspace == NULL makes the call allocate and free it on `stream`
+ * (stream-ordered allocation). y may alias base.
+ */
+int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
+                     const mont_ctx *ctx, uint32_t window, mp_red red, mp_algo algo,
+                     void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Measurement helper (no counterpart in the paper; it sets the roofline): runs one
+ * block of 1024 threads per SM executing `iters` rounds of an integer instruction
+ * mix and returns the issued rate per SM per clock (lanes x instructions / cycles,
+ * from clock64) and the SM clock implied by the kernel's wall time.
+ * mode 0: independent mad.lo.u32; 1: independent mad.hi.u32; 2: the library's 8x8
+ * block product (mad.lo.cc/madc.hi.cc chains, counts its 128 multiply-adds);
+ * 3: add.cc/addc.cc chains. Synchronous; allocates a small scratch buffer.
+ */
+int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPGPU_H */

@@ -1,0 +1,210 @@
+"""Python binding of libmpgpu (include/mpgpu.h): argument marshalling only.
+
+Every function takes torch CUDA tensors of dtype int32/uint32 (any 32-bit integer
+view), passes their device pointers and the current CUDA stream to the C ABI, and
+raises MpError on a non-zero status. All arithmetic runs in the library's CUDA
+kernels; there is no CPU fallback: importing on a machine without the built
+library raises ImportError.
+
+Names follow the C ABI: mp_mul, mp_sqr, mont_ctx_init (-> MontCtx), mont_mul,
+mont_sqr, modexp_consttime, mp_convert.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmpgpu.so")
+
+LAYOUT_INSTANCE_MAJOR, LAYOUT_INTERLEAVED = 0, 1
+ALGO_AUTO, ALGO_SCHOOLBOOK, ALGO_KARATSUBA = 0, 1, 2
+RED_TRUNCATED, RED_FULL = 0, 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmpgpu.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python paper_2410_18129_gb300/build.py")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp, _sz, _u32, _i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int
+_SIG = {
+    "mp_strerror": ([_i], ctypes.c_char_p),
+    "mp_max_bits": ([], _u32),
+    "mp_version": ([], ctypes.c_char_p),
+    "mp_convert": ([_vp, _i, _vp, _i, _sz, _u32, _vp], _i),
+    "mp_mul": ([_vp, _vp, _vp, _sz, _u32, _i, _i, _vp], _i),
+    "mp_sqr": ([_vp, _vp, _sz, _u32, _i, _i, _vp], _i),
+    "mont_ctx_init": ([ctypes.POINTER(_vp), _vp, _sz, _u32, _i, ctypes.POINTER(_sz), _vp], _i),
+    "mont_ctx_free": ([_vp], _i),
+    "mont_ctx_info": ([_vp, ctypes.POINTER(_sz), ctypes.POINTER(_u32), ctypes.POINTER(_i)], _i),
+    "mont_ctx_export": ([_vp, _i, _vp, _vp], _i),
+    "mont_mul": ([_vp, _vp, _vp, _vp, _i, _i, _vp], _i),
+    "mont_sqr": ([_vp, _vp, _vp, _i, _i, _vp], _i),
+    "modexp_workspace_bytes": ([_sz, _u32, _u32], _sz),
+    "modexp_consttime": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp, _sz, _vp], _i),
+    "mp_bench_imad": ([_i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp], _i),
+}
+for _name, (_args, _res) in _SIG.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIG)
+
+
+class MpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_lib.mp_strerror(status).decode()} ({status})")
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise MpError(st, where)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.element_size() != 4:
+        raise ValueError("expected a 32-bit integer tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def words(bits: int) -> int:
+    return (int(bits) + 31) // 32
+
+
+def max_bits() -> int:
+    return int(_lib.mp_max_bits())
+
+
+def version() -> str:
+    return _lib.mp_version().decode()
+
+
+def array_words(layout: int, batch: int, w: int) -> int:
+    """Words of an array of `batch` values of `w` words in `layout`."""
+    return ((w + 3) // 4) * 4 * batch if layout == LAYOUT_INTERLEAVED else w * batch
+
+
+def mp_convert(dst: torch.Tensor, dst_layout: int, src: torch.Tensor, src_layout: int, batch: int, w: int):
+    _check(_lib.mp_convert(_ptr(dst), dst_layout, _ptr(src), src_layout, batch, w, _stream()), "mp_convert")
+    return dst
+
+
+def mp_mul(c, a, b, batch: int, bits: int, layout: int = LAYOUT_INSTANCE_MAJOR, algo: int = ALGO_AUTO):
+    _check(_lib.mp_mul(_ptr(c), _ptr(a), _ptr(b), batch, bits, layout, algo, _stream()), "mp_mul")
+    return c
+
+
+def mp_sqr(c, a, batch: int, bits: int, layout: int = LAYOUT_INSTANCE_MAJOR, algo: int = ALGO_AUTO):
+    _check(_lib.mp_sqr(_ptr(c), _ptr(a), batch, bits, layout, algo, _stream()), "mp_sqr")
+    return c
+
+
+class MontCtx:
+    """Owns a mont_ctx (device copies of N, N', R mod N, R^2 mod N)."""
+
+    def __init__(self, N: torch.Tensor, batch: int, bits: int, layout: int = LAYOUT_INSTANCE_MAJOR):
+        h = ctypes.c_void_p()
+        bad = ctypes.c_size_t(0)
+        st = _lib.mont_ctx_init(ctypes.byref(h), _ptr(N), batch, bits, layout, ctypes.byref(bad), _stream())
+        if st == -3:
+            err = MpError(st, "mont_ctx_init")
+            err.bad_index = int(bad.value)
+            raise err
+        _check(st, "mont_ctx_init")
+        self.handle = h
+        self.batch, self.bits, self.layout = batch, bits, layout
+        self.n = words(bits)
+
+    def export(self, which: int) -> torch.Tensor:
+        out = torch.zeros(array_words(self.layout, self.batch, self.n), dtype=torch.int32, device="cuda")
+        _check(_lib.mont_ctx_export(self.handle, which, _ptr(out), _stream()), "mont_ctx_export")
+        return out
+
+    def free(self):
+        if self.handle:
+            _check(_lib.mont_ctx_free(self.handle), "mont_ctx_free")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                _lib.mont_ctx_free(self.handle)
+        except Exception:
+            pass
+
+
+def mont_ctx_init(N, batch: int, bits: int, layout: int = LAYOUT_INSTANCE_MAJOR) -> MontCtx:
+    return MontCtx(N, batch, bits, layout)
+
+
+def mont_mul(c, a, b, ctx: MontCtx, red: int = RED_TRUNCATED, algo: int = ALGO_AUTO):
+    _check(_lib.mont_mul(_ptr(c), _ptr(a), _ptr(b), ctx.handle, red, algo, _stream()), "mont_mul")
+    return c
+
+
+def mont_sqr(c, a, ctx: MontCtx, red: int = RED_TRUNCATED, algo: int = ALGO_AUTO):
+    _check(_lib.mont_sqr(_ptr(c), _ptr(a), ctx.handle, red, algo, _stream()), "mont_sqr")
+    return c
+
+
+def modexp_workspace_bytes(batch: int, bits: int, window: int) -> int:
+    return int(_lib.modexp_workspace_bytes(batch, bits, window))
+
+
+def modexp_consttime(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,
+                     red: int = RED_TRUNCATED, algo: int = ALGO_AUTO, workspace: torch.Tensor | None = None):
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.modexp_consttime(_ptr(y), _ptr(base), _ptr(exp), exp_bits, ctx.handle, window, red, algo,
+                                 _ptr(workspace), ws_bytes, _stream()), "modexp_consttime")
+    return y
+
+
+def bench_imad(mode: int, iters: int = 2000):
+    """(rate per SM per clock, implied SM MHz) of the integer microbenchmark `mode`."""
+    r, mhz = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.mp_bench_imad(mode, iters, ctypes.byref(r), ctypes.byref(mhz), _stream()), "mp_bench_imad")
+    return r.value, mhz.value
+
+
+# --------------------------------------------------------------------------- host helpers
+
+def to_device(x, device="cuda") -> torch.Tensor:
+    """numpy uint32 array -> int32 CUDA tensor with the same bits."""
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(x).view(np.int32)).to(device)
+
+
+def to_host(t: torch.Tensor):
+    import numpy as np
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def interleave(x):
+    """[batch, w] instance-major numpy -> flat interleaved numpy (host-side reshaping only)."""
+    import numpy as np
+    B, w = x.shape
+    c = (w + 3) // 4
+    pad = np.zeros((B, c * 4), np.uint32)
+    pad[:, :w] = x
+    return np.ascontiguousarray(pad.reshape(B, c, 4).transpose(1, 0, 2)).reshape(-1)
+
+
+def deinterleave(flat, batch: int, w: int):
+    import numpy as np
+    c = (w + 3) // 4
+    return np.ascontiguousarray(np.asarray(flat, np.uint32).reshape(c, batch, 4).transpose(1, 0, 2)
+                                ).reshape(batch, c * 4)[:, :w]

@@ -1,0 +1,406 @@
+// C ABI of the library (include/mpgpu.h): argument checks, shape dispatch,
+// Montgomery-context construction and the layout conversion kernel.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include "mp_kernels.cuh"
+#include "../../include/mpgpu.h"
+
+namespace mpg {
+ShapeOps shape_ops_2_4();
+ShapeOps shape_ops_4_4();
+ShapeOps shape_ops_4_8();
+ShapeOps shape_ops_8_8();
+ShapeOps shape_ops_8_12();
+ShapeOps shape_ops_8_16();
+ShapeOps shape_ops_8_18();
+}  // namespace mpg
+
+using namespace mpg;
+
+static constexpr uint32_t MAX_NP = 144;   // largest padded size: 8 threads x 18 words
+static constexpr uint32_t MAX_BITS = 32 * MAX_NP;
+
+// smallest shape whose padded size holds n words
+static const ShapeOps *shape_for(uint32_t n) {
+    static ShapeOps table[7];
+    static bool init = false;
+    if (!init) {
+        table[0] = shape_ops_2_4();
+        table[1] = shape_ops_4_4();
+        table[2] = shape_ops_4_8();
+        table[3] = shape_ops_8_8();
+        table[4] = shape_ops_8_12();
+        table[5] = shape_ops_8_16();
+        table[6] = shape_ops_8_18();
+        init = true;
+    }
+    for (auto &s : table)
+        if ((uint32_t)s.NP >= n) return &s;
+    return nullptr;
+}
+
+struct mont_ctx {
+    size_t batch;
+    uint32_t bits, n, np;
+    mp_layout layout;
+    const ShapeOps *shape;
+    uint32_t *mem;            // one allocation for everything below
+    uint32_t *N, *NI, *R1, *R2, *K;           // internal: interleaved, np words
+    uint32_t *NI_api, *R1_api, *R2_api, *N_api;  // API layout, n words
+    size_t api_words;         // words of one API array
+};
+
+static inline uint32_t words_for(uint32_t bits) { return (bits + 31u) / 32u; }
+static inline size_t api_array_words(mp_layout layout, size_t batch, uint32_t words) {
+    return layout == MP_LAYOUT_INTERLEAVED ? (size_t)((words + 3u) / 4u) * 4u * batch : (size_t)words * batch;
+}
+static inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+static inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" const char *mp_strerror(int st) {
+    switch (st) {
+        case MP_OK: return "ok";
+        case MP_ERR_ARG: return "invalid argument";
+        case MP_ERR_SIZE: return "operand size or window out of range";
+        case MP_ERR_EVEN_MODULUS: return "even modulus";
+        case MP_ERR_ALIGN: return "pointer not 16-byte aligned";
+        case MP_ERR_CUDA: return "CUDA error";
+        case MP_ERR_NOMEM: return "out of device memory or workspace too small";
+        case MP_ERR_UNIMPLEMENTED: return "not implemented";
+        case MP_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+extern "C" uint32_t mp_max_bits(void) { return MAX_BITS; }
+extern "C" const char *mp_version(void) { return "mpgpu 0.1 (sm_103a)"; }
+
+static int check_layout(mp_layout l) { return (l == MP_LAYOUT_INSTANCE_MAJOR || l == MP_LAYOUT_INTERLEAVED) ? MP_OK : MP_ERR_ARG; }
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? MP_OK : MP_ERR_CUDA; }
+
+// ------------------------------------------------------------------ layout conversion
+
+__global__ void k_convert(uint32_t *dst, int dl, const uint32_t *src, int sl, size_t batch, int words) {
+    // destination positions, padding words of an interleaved destination included
+    const size_t total = (dl == LAYOUT_IL) ? (size_t)((words + 3) / 4) * 4 * batch : batch * (size_t)words;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        // enumerate in destination order so that the stores are coalesced
+        size_t k;
+        int i;
+        if (dl == LAYOUT_IM) { k = x / (size_t)words; i = (int)(x % (size_t)words); }
+        else {
+            const size_t chunk = x / (4 * batch), r = x % (4 * batch);
+            k = r / 4;
+            i = (int)(chunk * 4 + r % 4);
+            if (i >= words) continue;
+        }
+        dst[widx(dl, k, i, words, batch)] = src[widx(sl, k, i, words, batch)];
+    }
+}
+
+static int launch_convert(uint32_t *dst, int dl, const uint32_t *src, int sl, size_t batch, int words, cudaStream_t st) {
+    size_t total = (dl == LAYOUT_IL) ? (size_t)((words + 3) / 4) * 4 * batch : (size_t)words * batch;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (blocks > 152u * 32u) blocks = 152u * 32u;
+    if (blocks == 0) blocks = 1;
+    k_convert<<<blocks, 256, 0, st>>>(dst, dl, src, sl, batch, words);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int mp_convert(uint32_t *dst, mp_layout dst_layout, const uint32_t *src, mp_layout src_layout,
+                          size_t batch, uint32_t words, void *stream) {
+    if (!dst || !src || batch == 0 || words == 0) return MP_ERR_ARG;
+    if (check_layout(dst_layout) || check_layout(src_layout)) return MP_ERR_ARG;
+    if ((dst_layout == MP_LAYOUT_INTERLEAVED && !aligned16(dst)) ||
+        (src_layout == MP_LAYOUT_INTERLEAVED && !aligned16(src)))
+        return MP_ERR_ALIGN;
+    if (dst_layout == src_layout)
+        return cuda_status(cudaMemcpyAsync(dst, src, api_array_words(dst_layout, batch, words) * 4,
+                                           cudaMemcpyDeviceToDevice, S(stream)));
+    return launch_convert(dst, (int)dst_layout, src, (int)src_layout, batch, (int)words, S(stream));
+}
+
+// ------------------------------------------------------------------ products
+
+static int check_common(size_t batch, uint32_t bits, mp_layout layout, mp_algo algo) {
+    if (batch == 0) return MP_ERR_ARG;
+    if (check_layout(layout)) return MP_ERR_ARG;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    return MP_OK;
+}
+
+static int product(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,
+                   mp_layout layout, mp_algo algo, bool square, void *stream) {
+    if (!c || !a || (!square && !b)) return MP_ERR_ARG;
+    int st = check_common(batch, bits, layout, algo);
+    if (st) return st;
+    if (layout == MP_LAYOUT_INTERLEAVED && (!aligned16(c) || !aligned16(a) || (!square && !aligned16(b))))
+        return MP_ERR_ALIGN;
+    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    const uint32_t n = words_for(bits);
+    const ShapeOps *sh = shape_for(n);
+    if (!sh) return MP_ERR_SIZE;
+    KArgs A{};
+    A.out = c; A.a = a; A.b = square ? a : b;
+    A.batch = batch; A.n = (int)n; A.layout = (int)layout; A.square = square ? 1 : 0;
+    return cuda_status(sh->mul(A, S(stream)));
+}
+
+extern "C" int mp_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,
+                      mp_layout layout, mp_algo algo, void *stream) {
+    return product(c, a, b, batch, bits, layout, algo, false, stream);
+}
+
+extern "C" int mp_sqr(uint32_t *c, const uint32_t *a, size_t batch, uint32_t bits, mp_layout layout,
+                      mp_algo algo, void *stream) {
+    return product(c, a, nullptr, batch, bits, layout, algo, true, stream);
+}
+
+// ------------------------------------------------------------------ Montgomery context
+
+// x <- 2x mod N (x < N), np words, select without a branch
+__device__ void dbl_mod(uint32_t *x, const uint32_t *N, int np) {
+    uint32_t carry = 0;
+    for (int i = 0; i < np; ++i) {
+        const uint32_t v = x[i];
+        x[i] = (v << 1) | carry;
+        carry = v >> 31;
+    }
+    uint32_t d[MAX_NP];
+    uint32_t borrow = 0;
+    for (int i = 0; i < np; ++i) {
+        const uint64_t t = (uint64_t)x[i] - N[i] - borrow;
+        d[i] = (uint32_t)t;
+        borrow = (uint32_t)(t >> 63);
+    }
+    const uint32_t m = 0u - (carry | (borrow ^ 1u));
+    for (int i = 0; i < np; ++i) x[i] = (d[i] & m) | (x[i] & ~m);
+}
+
+// One thread per modulus: N' by word-level Hensel lifting, powers of two mod N by
+// modular doubling. Not on the hot path (runs once per modulus).
+__global__ void k_ctx_init(const uint32_t *Napi, int layout, size_t batch, int n, int np, uint32_t *N,
+                           uint32_t *NI, uint32_t *R1, uint32_t *R2, uint32_t *K, uint32_t *NI_api,
+                           uint32_t *R1_api, uint32_t *R2_api, uint32_t *N_api, unsigned long long *bad) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= batch) return;
+    uint32_t nn[MAX_NP], x[MAX_NP], p[MAX_NP], r1[MAX_NP];
+    for (int i = 0; i < np; ++i) nn[i] = (i < n) ? Napi[widx(layout, k, i, n, batch)] : 0u;
+    for (int i = 0; i < n; ++i) N_api[widx(layout, k, i, n, batch)] = nn[i];
+    if ((nn[0] & 1u) == 0u) {
+        atomicMin(bad, (unsigned long long)k);
+        return;
+    }
+    // 32-bit inverse of N0 by Newton's iteration y <- y (2 - N0 y): 3, 6, 12, 24, 48 bits
+    uint32_t y = nn[0];
+    for (int it = 0; it < 4; ++it) y *= 2u - nn[0] * y;
+    const uint32_t n0p = 0u - y;   // -N0^{-1} mod 2^32
+    // word-level lifting: keep P = N*x + 1 mod W^np; x_i = P_i * n0p clears word i
+    for (int i = 0; i < np; ++i) { p[i] = 0u; x[i] = 0u; }
+    p[0] = 1u;
+    for (int i = 0; i < np; ++i) {
+        const uint32_t xi = p[i] * n0p;
+        x[i] = xi;
+        uint64_t c = 0;
+        for (int j = 0; i + j < np; ++j) {
+            c += (uint64_t)xi * nn[j] + p[i + j];
+            p[i + j] = (uint32_t)c;
+            c >>= 32;
+        }
+    }
+    auto put_il = [&](uint32_t *dst, const uint32_t *src) {
+        for (int i = 0; i < np; ++i) dst[widx(LAYOUT_IL, k, i, np, batch)] = src[i];
+    };
+    auto put_api = [&](uint32_t *dst, const uint32_t *src) {
+        for (int i = 0; i < n; ++i) dst[widx(layout, k, i, n, batch)] = src[i];
+    };
+    put_il(N, nn);
+    put_il(NI, x);
+    put_api(NI_api, x);   // (-N)^-1 mod W^n is the low n words of (-N)^-1 mod W^np
+    // powers of two: start at 1 and double
+    for (int i = 0; i < np; ++i) p[i] = 0u;
+    p[0] = 1u;
+    for (int d = 0; d < 32 * n; ++d) dbl_mod(p, nn, np);
+    put_api(R1_api, p);                               // W^n mod N
+    for (int i = 0; i < np; ++i) r1[i] = p[i];
+    for (int d = 0; d < 32 * n; ++d) dbl_mod(r1, nn, np);
+    put_api(R2_api, r1);                              // W^2n mod N
+    for (int d = 0; d < 32 * (np - n); ++d) dbl_mod(p, nn, np);
+    put_il(R1, p);                                    // W^np mod N
+    for (int i = 0; i < np; ++i) r1[i] = p[i];
+    for (int d = 0; d < 32 * (np - n); ++d) dbl_mod(r1, nn, np);
+    put_il(K, r1);                                    // W^(2np-n) mod N
+    for (int d = 0; d < 32 * np; ++d) dbl_mod(p, nn, np);
+    put_il(R2, p);                                    // W^2np mod N
+}
+
+extern "C" int mont_ctx_init(mont_ctx **out, const uint32_t *N, size_t batch, uint32_t bits, mp_layout layout,
+                             size_t *bad_index, void *stream) {
+    if (!out || !N || batch == 0) return MP_ERR_ARG;
+    *out = nullptr;
+    if (check_layout(layout)) return MP_ERR_ARG;
+    if (bits < 2 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (layout == MP_LAYOUT_INTERLEAVED && !aligned16(N)) return MP_ERR_ALIGN;
+    const uint32_t n = words_for(bits);
+    const ShapeOps *sh = shape_for(n);
+    if (!sh) return MP_ERR_SIZE;
+    mont_ctx *c = new (std::nothrow) mont_ctx{};
+    if (!c) return MP_ERR_NOMEM;
+    c->batch = batch; c->bits = bits; c->n = n; c->np = (uint32_t)sh->NP; c->layout = layout; c->shape = sh;
+    c->api_words = api_array_words(layout, batch, n);
+    const size_t internal = (size_t)c->np * batch;
+    const size_t total = 5 * internal + 4 * c->api_words + 4;   // +4: the error word (8 bytes, kept aligned)
+    if (cudaMalloc(&c->mem, total * 4) != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return MP_ERR_NOMEM;
+    }
+    uint32_t *p = c->mem;
+    c->N = p; p += internal;
+    c->NI = p; p += internal;
+    c->R1 = p; p += internal;
+    c->R2 = p; p += internal;
+    c->K = p; p += internal;
+    c->NI_api = p; p += c->api_words;
+    c->R1_api = p; p += c->api_words;
+    c->R2_api = p; p += c->api_words;
+    c->N_api = p; p += c->api_words;
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(p);
+    cudaStream_t st = S(stream);
+    int rc = MP_OK;
+    const unsigned long long none = ~0ull;
+    unsigned long long first = none;
+    do {
+        if (cudaMemcpyAsync(bad, &none, 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ERR_CUDA; break; }
+        if (cudaMemsetAsync(c->mem, 0, 5 * internal * 4, st) != cudaSuccess) { rc = MP_ERR_CUDA; break; }
+        const unsigned blocks = (unsigned)((batch + 127) / 128);
+        k_ctx_init<<<blocks, 128, 0, st>>>(N, (int)layout, batch, (int)n, (int)c->np, c->N, c->NI, c->R1, c->R2,
+                                           c->K, c->NI_api, c->R1_api, c->R2_api, c->N_api, bad);
+        if (cudaGetLastError() != cudaSuccess) { rc = MP_ERR_CUDA; break; }
+        if (cudaMemcpyAsync(&first, bad, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = MP_ERR_CUDA; break; }
+        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MP_ERR_CUDA; break; }
+        if (first != none) {
+            if (bad_index) *bad_index = (size_t)first;
+            rc = MP_ERR_EVEN_MODULUS;
+        }
+    } while (0);
+    if (rc != MP_OK) {
+        cudaFree(c->mem);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return MP_OK;
+}
+
+extern "C" int mont_ctx_free(mont_ctx *c) {
+    if (!c) return MP_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t f = cudaFree(c->mem);
+    delete c;
+    return (e == cudaSuccess && f == cudaSuccess) ? MP_OK : MP_ERR_CUDA;
+}
+
+extern "C" int mont_ctx_info(const mont_ctx *c, size_t *batch, uint32_t *bits, mp_layout *layout) {
+    if (!c) return MP_ERR_ARG;
+    if (batch) *batch = c->batch;
+    if (bits) *bits = c->bits;
+    if (layout) *layout = c->layout;
+    return MP_OK;
+}
+
+extern "C" int mont_ctx_export(const mont_ctx *c, int which, uint32_t *dst, void *stream) {
+    if (!c || !dst) return MP_ERR_ARG;
+    const uint32_t *src = which == 0 ? c->NI_api : which == 1 ? c->R1_api : which == 2 ? c->R2_api
+                        : which == 3 ? c->N_api : nullptr;
+    if (!src) return MP_ERR_ARG;
+    if (c->layout == MP_LAYOUT_INTERLEAVED && !aligned16(dst)) return MP_ERR_ALIGN;
+    return cuda_status(cudaMemcpyAsync(dst, src, c->api_words * 4, cudaMemcpyDeviceToDevice, S(stream)));
+}
+
+// ------------------------------------------------------------------ Montgomery products
+
+static void fill_ctx_args(KArgs &A, const mont_ctx *c) {
+    A.N = c->N; A.NI = c->NI; A.R1 = c->R1; A.R2 = c->R2; A.K = c->K;
+    A.batch = c->batch; A.n = (int)c->n; A.layout = (int)c->layout;
+    A.correct = (c->n != c->np) ? 1 : 0;
+}
+
+static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
+                       mp_algo algo, bool square, void *stream) {
+    if (!out || !a || (!square && !b) || !c) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
+    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(out) || !aligned16(a) || (!square && !aligned16(b))))
+        return MP_ERR_ALIGN;
+    KArgs A{};
+    fill_ctx_args(A, c);
+    A.out = out; A.a = a; A.b = square ? a : b; A.red = (int)red; A.square = square ? 1 : 0;
+    return cuda_status(c->shape->mont(A, S(stream)));
+}
+
+extern "C" int mont_mul(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
+                        mp_algo algo, void *stream) {
+    return mont_common(out, a, b, c, red, algo, false, stream);
+}
+
+extern "C" int mont_sqr(uint32_t *out, const uint32_t *a, const mont_ctx *c, mp_red red, mp_algo algo,
+                        void *stream) {
+    return mont_common(out, a, nullptr, c, red, algo, true, stream);
+}
+
+// ------------------------------------------------------------------ exponentiation
+
+static uint32_t tuned_window(uint32_t bits) { return bits <= 1024 ? 4u : bits <= 3072 ? 5u : 6u; }
+
+extern "C" size_t modexp_workspace_bytes(size_t batch, uint32_t bits, uint32_t window) {
+    if (bits == 0 || bits > MAX_BITS) return 0;
+    if (window == 0) window = tuned_window(bits);
+    if (window > 6) return 0;
+    const ShapeOps *sh = shape_for(words_for(bits));
+    if (!sh) return 0;
+    return ((size_t)1 << window) * (size_t)sh->NP * batch * 4;
+}
+
+extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
+                                const mont_ctx *c, uint32_t window, mp_red red, mp_algo algo, void *workspace,
+                                size_t workspace_bytes, void *stream) {
+    if (!y || !base || !c || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
+    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    if (window == 0) window = tuned_window(c->bits);
+    if (window > 6) return MP_ERR_SIZE;
+    if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp))))
+        return MP_ERR_ALIGN;
+    const size_t need = modexp_workspace_bytes(c->batch, c->bits, window);
+    cudaStream_t st = S(stream);
+    void *ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (!aligned16(ws)) return MP_ERR_ALIGN;
+        if (workspace_bytes < need) return MP_ERR_NOMEM;
+    } else {
+        if (cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            return MP_ERR_NOMEM;
+        }
+        own = true;
+    }
+    KArgs A{};
+    fill_ctx_args(A, c);
+    A.out = y; A.a = base; A.e = exp; A.table = reinterpret_cast<uint32_t *>(ws);
+    A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
+    A.red = (int)red;
+    int rc = cuda_status(c->shape->modexp(A, st));
+    if (own) {
+        if (cudaFreeAsync(ws, st) != cudaSuccess && rc == MP_OK) rc = MP_ERR_CUDA;
+    }
+    return rc;
+}

@@ -1,0 +1,543 @@
+// Group-cooperative multi-precision arithmetic: one instance per group of G
+// threads of a warp, each thread holding M consecutive words of every operand.
+//
+// Products are computed as sums of B x B "block products" (B = M for full
+// products, B = M/2 for the truncated halves). Output columns are cut into
+// slots of B words; every thread owns two slots chosen so that all threads do
+// the same number of block products (balanced even for the triangular low and
+// high halves), accumulates each slot in registers, and parks the raw slot
+// sums in shared memory. A carry-resolution pass then turns the overlapping
+// slot sums into words: each slot adds the spill of its predecessor, passes
+// on a small overflow word, and the remaining one-bit carries are resolved
+// for the whole group at once with a warp ballot (carry-lookahead).
+//
+// Montgomery product (Alg. 5 / Alg. 6 in 32-bit words, R = 2^(32*NP)):
+//   1. T = X*Y            (Alg. 1) or T = X^2 (Alg. 2)
+//   2. q = T_lo * N' mod R          (low half only)
+//   3a. truncated: C = T_hi + floor(q*N/R) + c_add           (Alg. 6, Thm. 1, Thm. 2)
+//   3b. classical: C = (T + q*N) / R                         (Alg. 3 with B_fma)
+//   4. C >= N ? C - N : C  (constant-time select)
+// No branch or address depends on operand values; branches on the thread
+// index inside the group (which slot a thread owns) are public.
+#pragma once
+#include "mp_limb.cuh"
+
+namespace mpg {
+
+template <int G_, int M_>
+struct Shape {
+    static constexpr int G = G_;           // threads per instance
+    static constexpr int M = M_;           // words per thread
+    static constexpr int NP = G * M;       // words per operand (padded size)
+    static constexpr int H = M / 2;        // half-block width of the truncated products
+    static constexpr int A1 = 2 * M + 2;   // slot accumulator words, full blocks
+    static constexpr int A2 = 2 * H + 2;   // slot accumulator words, half blocks
+    static_assert(G >= 2 && G <= 16 && (G & (G - 1)) == 0, "G must be 2, 4, 8 or 16");
+    static_assert(M >= 4 && M % 2 == 0, "M must be even and >= 4");
+    // per-instance shared memory map (32-bit words)
+    static constexpr int OFF_X = 0;               // operand / result
+    static constexpr int OFF_Y = NP;              // operand (Y and Q together hold the squares of X)
+    static constexpr int OFF_Q = 2 * NP;          // q
+    static constexpr int OFF_N = 3 * NP;          // modulus
+    static constexpr int OFF_NI = 4 * NP;         // N' = (-N)^-1 mod R
+    static constexpr int OFF_T = 5 * NP;          // T (2*NP words)
+    static constexpr int OFF_P = 7 * NP;          // raw slot sums
+    static constexpr int OFF_OV = OFF_P + 2 * G * A1;   // overflow words (2 per slot)
+    static constexpr int OFF_Z = OFF_OV + 4 * G;        // M zero words
+    static constexpr int WORDS_RAW = OFF_Z + M;
+    static constexpr int WORDS = (WORDS_RAW + 3) & ~3;  // keep every instance 16-byte aligned
+};
+
+// Per-thread view of its group.
+template <class S>
+struct Grp {
+    uint32_t *sm;   // this instance's shared words
+    int t;          // thread index in the group
+    int gbase;      // warp lane of thread 0 of the group
+    MPG_DI uint32_t *X() const { return sm + S::OFF_X; }
+    MPG_DI uint32_t *Y() const { return sm + S::OFF_Y; }
+    MPG_DI uint32_t *Q() const { return sm + S::OFF_Q; }
+    MPG_DI uint32_t *N() const { return sm + S::OFF_N; }
+    MPG_DI uint32_t *NI() const { return sm + S::OFF_NI; }
+    MPG_DI uint32_t *T() const { return sm + S::OFF_T; }
+    MPG_DI uint32_t *P() const { return sm + S::OFF_P; }
+    MPG_DI uint32_t *OV() const { return sm + S::OFF_OV; }
+    MPG_DI uint32_t *Z() const { return sm + S::OFF_Z; }
+    // this group's bits of a warp ballot
+    MPG_DI uint32_t gbits(bool pred) const {
+        return (__ballot_sync(0xffffffffu, pred) >> gbase) & ((1u << S::G) - 1u);
+    }
+};
+
+MPG_DI void gsync() { __syncwarp(); }
+
+// ------------------------------------------------------------------ shared-memory blocks
+
+template <int K>
+MPG_DI void lds(uint32_t (&x)[K], const uint32_t *p) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < K / 4; ++k) {
+            uint4 v = reinterpret_cast<const uint4 *>(p)[k];
+            x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < K / 2; ++k) {
+            uint2 v = reinterpret_cast<const uint2 *>(p)[k];
+            x[2 * k] = v.x; x[2 * k + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) x[k] = p[k];
+    }
+}
+
+template <int K>
+MPG_DI void sts(uint32_t *p, const uint32_t (&x)[K]) {
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < K / 4; ++k)
+            reinterpret_cast<uint4 *>(p)[k] = make_uint4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < K / 2; ++k) reinterpret_cast<uint2 *>(p)[k] = make_uint2(x[2 * k], x[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] = x[k];
+    }
+}
+
+template <int K>
+MPG_DI void zero(uint32_t (&x)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) x[k] = 0u;
+}
+
+// V += X_u * Y_v for B-word blocks at p and q
+template <int B>
+MPG_DI void mac_block(uint32_t (&V)[2 * B + 2], const uint32_t *xp, const uint32_t *yp) {
+    uint32_t x[B], y[B], P[2 * B];
+    lds<B>(x, xp);
+    lds<B>(y, yp);
+    block_mul<B>(P, x, y);
+    acc_add<B>(V, P);
+}
+
+// ------------------------------------------------------------------ carry resolution
+
+enum SlotPattern { PAT_SEQ = 0, PAT_ZIGZAG = 1, PAT_ONE = 2 };
+
+template <int G, int PAT>
+MPG_DI int slot_of(int t, int k) {
+    if constexpr (PAT == PAT_SEQ) return k ? G + t : t;
+    else if constexpr (PAT == PAT_ZIGZAG) return k ? 2 * G - 1 - t : t;
+    else return t;
+}
+
+// group ballot bits (bit t = lane t of the group) -> bits indexed by slot number
+template <int G, int PAT>
+MPG_DI uint64_t slot_mask(uint32_t bitsA, uint32_t bitsB) {
+    if constexpr (PAT == PAT_SEQ) return (uint64_t)bitsA | ((uint64_t)bitsB << G);
+    else if constexpr (PAT == PAT_ZIGZAG) return (uint64_t)bitsA | ((uint64_t)(__brev(bitsB) >> (32 - 2 * G)));
+    else return (uint64_t)bitsA;
+}
+
+struct NoXform {
+    template <int A>
+    MPG_DI void operator()(int, uint32_t (&)[A]) const {}
+};
+
+// Turn the raw slot sums P[s] (A = 2B+2 words each, slot s covering output words
+// [s*B, s*B+B) and spilling into the next slots) into words OUT[s*B..s*B+B).
+// in0: B+2 words added below slot 0 (a carry coming from outside). xf may rewrite a
+// slot sum first (add an addend, double it ...). Returns the low word of everything
+// above the last slot (its own spill and overflow plus the resolved carry).
+template <class S, int B, int PAT, class XF>
+MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF &xf, uint32_t *OUT) {
+    constexpr int G = S::G;
+    constexpr int A = 2 * B + 2;
+    constexpr int NS = (PAT == PAT_ONE) ? 1 : 2;
+    constexpr int NSLOT = (PAT == PAT_ONE) ? G : 2 * G;
+    uint32_t *Pm = g.P();
+    uint32_t *OV = g.OV();
+    uint32_t lo[NS][B];
+    uint32_t top = 0u;   // words at and above the last slot: its own spill + overflow (owner only)
+
+    // 1. optional per-slot rewrite; keep the low B words
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        uint32_t V[A];
+        lds<A>(V, Pm + s * A);
+        xf(s, V);
+        sts<A>(Pm + s * A, V);
+#pragma unroll
+        for (int j = 0; j < B; ++j) lo[k][j] = V[j];
+        if (s == NSLOT - 1) top = V[B];
+    }
+    gsync();
+    // 2. add the predecessor's spill (its words B..2B+1); overflow goes to OV
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        uint32_t x[B + 2];
+        if (s == 0) {
+#pragma unroll
+            for (int j = 0; j < B + 2; ++j) x[j] = in0[j];
+        } else {
+            const uint32_t *sp = Pm + (s - 1) * A + B;
+#pragma unroll
+            for (int j = 0; j < B + 2; ++j) x[j] = sp[j];
+        }
+        add_cc(x[0], lo[k][0]);
+#pragma unroll
+        for (int j = 1; j < B; ++j) addc_cc(x[j], lo[k][j]);
+        addc_cc(x[B], 0u);
+        addc(x[B + 1], 0u);
+#pragma unroll
+        for (int j = 0; j < B; ++j) lo[k][j] = x[j];
+        OV[2 * s] = x[B];
+        OV[2 * s + 1] = x[B + 1];
+        if (s == NSLOT - 1) top += x[B];
+    }
+    gsync();
+    // 3. add the predecessor's overflow: leaves a 0/1 carry per slot
+    uint32_t cgen[NS], cprop[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        uint32_t o0 = 0u, o1 = 0u;
+        if (s > 0) { o0 = OV[2 * s - 2]; o1 = OV[2 * s - 1]; }
+        add_cc(lo[k][0], o0);
+        addc_cc(lo[k][1], o1);
+#pragma unroll
+        for (int j = 2; j < B; ++j) addc_cc(lo[k][j], 0u);
+        cgen[k] = addc_get();
+        uint32_t all = lo[k][0];
+#pragma unroll
+        for (int j = 1; j < B; ++j) all &= lo[k][j];
+        cprop[k] = (all == 0xffffffffu) ? 1u : 0u;
+    }
+    // 4. carry-lookahead over the slots: carry into slot s = bit s of ((P + 2G) ^ P)
+    const uint32_t gA = g.gbits(cgen[0] != 0u), pA = g.gbits(cprop[0] != 0u);
+    uint32_t gB = 0u, pB = 0u;
+    if constexpr (NS == 2) { gB = g.gbits(cgen[NS - 1] != 0u); pB = g.gbits(cprop[NS - 1] != 0u); }
+    const uint64_t Gm = slot_mask<G, PAT>(gA, gB);
+    const uint64_t Pmask = slot_mask<G, PAT>(pA, pB);
+    const uint64_t cin = (Pmask + (Gm << 1)) ^ Pmask;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        add_word<B>(lo[k], (uint32_t)(cin >> s) & 1u);
+        sts<B>(OUT + s * B, lo[k]);
+    }
+    // the carry out of the last slot; callers use it only where the value above it is 0 or 1
+    constexpr int owner = (PAT == PAT_ZIGZAG) ? 0 : G - 1;
+    top = __shfl_sync(0xffffffffu, top, g.gbase + owner);
+    gsync();
+    return top + ((uint32_t)(cin >> NSLOT) & 1u);
+}
+
+// ------------------------------------------------------------------ products
+
+// T = X * Y (2*NP words). Full blocks: thread t owns slots t and G+t and computes
+// X_j * Y_{(t-j) mod G} for j = 0..G-1 (G block products for every thread).
+template <class S>
+MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *T) {
+    constexpr int G = S::G, M = S::M, A = S::A1;
+    uint32_t V[A];
+    zero<A>(V);
+    for (int j = 0; j < G; ++j) {
+        const int v = (g.t - j) & (G - 1);
+        mac_block<M>(V, X + j * M, Y + v * M);
+        if (j == g.t) {
+            sts<A>(g.P() + g.t * A, V);
+            zero<A>(V);
+        }
+    }
+    sts<A>(g.P() + (G + g.t) * A, V);
+    gsync();
+    uint32_t in0[M + 2];
+    zero<M + 2>(in0);
+    resolve<S, M, PAT_SEQ>(g, in0, NoXform{}, T);
+}
+
+// slot sums of squaring: V = 2 * (cross products) + (squares of the blocks)
+template <class S>
+struct SqrXform {
+    const uint32_t *D;
+    template <int A>
+    MPG_DI void operator()(int s, uint32_t (&V)[A]) const {
+        constexpr int M = S::M;
+#pragma unroll
+        for (int k = A - 1; k > 0; --k) V[k] = __funnelshift_l(V[k - 1], V[k], 1);
+        V[0] <<= 1;
+        uint32_t d[M];
+        lds<M>(d, D + s * M);
+        add_cc(V[0], d[0]);
+#pragma unroll
+        for (int j = 1; j < M; ++j) addc_cc(V[j], d[j]);
+#pragma unroll
+        for (int j = M; j < A - 1; ++j) addc_cc(V[j], 0u);
+        addc(V[A - 1], 0u);
+    }
+};
+
+// T = X^2 (Alg. 2 structure): squares of the G blocks (one per thread, written
+// side by side to D, 2*NP words) plus twice the cross products X_u X_v, u < v.
+// Thread t owns slots t and G+t; slot s gets the pairs u < v with u + v = s.
+template <class S>
+MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t *T) {
+    constexpr int G = S::G, M = S::M, A = S::A1;
+    {
+        uint32_t x[M], P[2 * M];
+        lds<M>(x, X + g.t * M);
+        block_mul<M>(P, x, x);
+        sts<2 * M>(D + 2 * g.t * M, P);
+    }
+    const int nA = (g.t + 1) >> 1;              // pairs u < v with u + v = t
+    const int nB = ((G - g.t + 1) >> 1) - 1;    // pairs with u + v = G + t
+    constexpr int K = G / 2;                    // max of nA + nB over the group
+    uint32_t V[A];
+    zero<A>(V);
+    bool a_done = false;
+    for (int j = 0; j < K; ++j) {
+        if (j == nA) {
+            sts<A>(g.P() + g.t * A, V);
+            zero<A>(V);
+            a_done = true;
+        }
+        int u, v;
+        if (j < nA) { u = j; v = g.t - j; }
+        else { u = g.t + 1 + (j - nA); v = G + g.t - u; }
+        const bool live = j < nA + nB;
+        mac_block<M>(V, X + (live ? u : 0) * M, live ? X + v * M : g.Z());
+    }
+    if (!a_done) {
+        sts<A>(g.P() + g.t * A, V);
+        zero<A>(V);
+    }
+    sts<A>(g.P() + (G + g.t) * A, V);
+    gsync();
+    uint32_t in0[M + 2];
+    zero<M + 2>(in0);
+    resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{D}, T);
+}
+
+// Q = (X * Y) mod W^NP with half blocks (H words, 2G of them). Thread t owns
+// slots t and 2G-1-t: t+1 and 2G-t block products, 2G+1 for every thread.
+template <class S>
+MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
+    constexpr int G = S::G, H = S::H, A = S::A2;
+    uint32_t V[A];
+    zero<A>(V);
+    for (int j = 0; j <= 2 * G; ++j) {
+        int u, v;
+        if (j <= g.t) { u = j; v = g.t - j; }
+        else { u = j - g.t - 1; v = 2 * G - j; }
+        mac_block<H>(V, X + u * H, Y + v * H);
+        if (j == g.t) {
+            sts<A>(g.P() + g.t * A, V);
+            zero<A>(V);
+        }
+    }
+    sts<A>(g.P() + (2 * G - 1 - g.t) * A, V);
+    gsync();
+    uint32_t in0[H + 2];
+    zero<H + 2>(in0);
+    resolve<S, H, PAT_ZIGZAG>(g, in0, NoXform{}, Q);
+}
+
+template <int B>
+struct AddendXform {
+    const uint32_t *Add;   // B words per slot
+    template <int A>
+    MPG_DI void operator()(int s, uint32_t (&V)[A]) const {
+        uint32_t d[B];
+        lds<B>(d, Add + s * B);
+        add_cc(V[0], d[0]);
+#pragma unroll
+        for (int j = 1; j < B; ++j) addc_cc(V[j], d[j]);
+#pragma unroll
+        for (int j = B; j < A - 1; ++j) addc_cc(V[j], 0u);
+        addc(V[A - 1], 0u);
+    }
+};
+
+// Z += the part of one H x H block product X_u*Y_v (u + v = 2G-1, so its local
+// column c sits at global column NP-H+c) that Thm. 2 needs: lo halves of the pairs
+// with i+j >= H-1 at word i+j-(H-1), hi halves of the pairs with i+j >= H-2 at word
+// i+j-(H-2). Word 0 of Z is global column NP-1.
+template <int H>
+MPG_DI void tri_mac(uint32_t (&Z)[H + 3], const uint32_t *xp, const uint32_t *yp) {
+    uint32_t x[H], y[H];
+    lds<H>(x, xp);
+    lds<H>(y, yp);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const int jl = (H - 1 - i > 0) ? H - 1 - i : 0;
+#pragma unroll
+        for (int j = jl; j < H; ++j) {
+            if (j == jl) mad_lo_cc(Z[i + j - H + 1], x[i], y[j]);
+            else madc_lo_cc(Z[i + j - H + 1], x[i], y[j]);
+        }
+#pragma unroll
+        for (int p = i + 1; p < H + 3; ++p) addc_cc(Z[p], 0u);
+        const int jh = (H - 2 - i > 0) ? H - 2 - i : 0;
+#pragma unroll
+        for (int j = jh; j < H; ++j) {
+            if (j == jh) mad_hi_cc(Z[i + j - H + 2], x[i], y[j]);
+            else madc_hi_cc(Z[i + j - H + 2], x[i], y[j]);
+        }
+#pragma unroll
+        for (int p = i + 2; p < H + 3; ++p) addc_cc(Z[p], 0u);
+    }
+}
+
+// Truncated high half (Alg. 6 lines 2-4 with Thm. 1 and Thm. 2), computing
+//   C = floor(T / R) + floor(q*N / R) + c_add            (NP words + carry out)
+// from only the partial products of q*N of weight >= NP-1 (lo halves) and
+// >= NP-2 (hi halves):
+//   * block products with u + v >= 2G (all their columns are >= NP) go to the
+//     H-word output slots h = u+v-2G (slot h covers words NP + h*H ...);
+//   * the blocks on the diagonal u + v = 2G-1 contribute their upper triangle
+//     (tri_mac) and the blocks on u + v = 2G-2 their corner hi half (column NP-2)
+//     to a small accumulator Z whose word 0 is column NP-1 (the sum S of Eq. qn);
+//   * the carry into column NP-1 from below is unknown, but word NP-1 of q*N is
+//     known: it is L = ((-T) mod R)[NP-1] (Thm. 1: T + qN = 0 mod R). Hence the
+//     carry out of column NP-1 is floor(Z / W) plus one exactly when L < Z[0].
+template <class S>
+MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, const uint32_t *T,
+                            uint32_t c_add, uint32_t low_zero, uint32_t *C) {
+    constexpr int G = S::G, H = S::H, A = S::A2, NP = S::NP;
+    // column NP-1 and the hi halves that reach it: thread t takes diagonal blocks u = 2t, 2t+1
+    uint32_t Z[H + 3];
+    zero<H + 3>(Z);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int u = 2 * g.t + j;
+        tri_mac<H>(Z, Qs + u * H, Ns + (2 * G - 1 - u) * H);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {   // corners of the blocks u + v = 2G-2 (2G-1 of them)
+        const int u = 2 * g.t + j;
+        const bool live = u <= 2 * G - 2;
+        const uint32_t xq = Qs[u * H + H - 1];
+        const uint32_t yn = live ? Ns[(2 * G - 2 - u) * H + H - 1] : 0u;
+        add_word<H + 3>(Z, __umulhi(xq, yn));
+    }
+    // output slots: A = t (absolute 2G+t), B = 2G-1-t (absolute 4G-1-t)
+    uint32_t V[A];
+    zero<A>(V);
+    const int nA = 2 * G - 1 - g.t;
+    for (int j = 0; j < 2 * G - 1; ++j) {
+        int u, v;
+        if (j < nA) { u = g.t + 1 + j; v = 2 * G + g.t - u; }
+        else { u = j + 1; v = 4 * G - 2 - g.t - j; }
+        mac_block<H>(V, Qs + u * H, Ns + v * H);
+        if (j == nA - 1) {
+            sts<A>(g.P() + g.t * A, V);
+            zero<A>(V);
+        }
+    }
+    sts<A>(g.P() + (2 * G - 1 - g.t) * A, V);
+    // sum Z over the group (butterfly; every lane gets the total)
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        uint32_t o[H + 3];
+#pragma unroll
+        for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
+        add_n<H + 3>(Z, o);
+    }
+    // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
+    const uint32_t L = ~T[NP - 1] + low_zero;
+    const uint32_t extra = (uint32_t)(((uint64_t)L - (uint64_t)Z[0]) >> 63);   // [L < Z[0]]
+    uint32_t in0[H + 2];
+#pragma unroll
+    for (int j = 0; j < H + 2; ++j) in0[j] = Z[1 + j];
+    add_word<H + 2>(in0, extra + c_add);
+    gsync();
+    return resolve<S, H, PAT_ZIGZAG>(g, in0, AddendXform<H>{T + NP}, C);
+}
+
+// Classical reduction: T + q*N over all 2*NP words (B_fma), result in T.
+// Returns the carry out of the top word (C = T[NP..2NP) + carry * R).
+template <class S>
+MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
+    constexpr int G = S::G, M = S::M, A = S::A1;
+    uint32_t V[A];
+    zero<A>(V);
+    for (int j = 0; j < G; ++j) {
+        const int v = (g.t - j) & (G - 1);
+        mac_block<M>(V, Qs + j * M, Ns + v * M);
+        if (j == g.t) {
+            sts<A>(g.P() + g.t * A, V);
+            zero<A>(V);
+        }
+    }
+    sts<A>(g.P() + (G + g.t) * A, V);
+    gsync();
+    uint32_t in0[M + 2];
+    zero<M + 2>(in0);
+    return resolve<S, M, PAT_SEQ>(g, in0, AddendXform<M>{T}, T);
+}
+
+// OUT = (carry*R + C >= N) ? C - N : C, constant time. Borrows are resolved across
+// the group with the same lookahead (a slot equal to N's propagates a borrow).
+template <class S>
+MPG_DI void cond_sub(const Grp<S> &g, const uint32_t *C, uint32_t carry, const uint32_t *Ns, uint32_t *OUT) {
+    constexpr int G = S::G, M = S::M;
+    uint32_t c[M], nn[M], d[M];
+    lds<M>(c, C + g.t * M);
+    lds<M>(nn, Ns + g.t * M);
+    uint32_t eq = 0u;
+#pragma unroll
+    for (int j = 0; j < M; ++j) { d[j] = c[j]; eq |= c[j] ^ nn[j]; }
+    const uint32_t bgen = sub_n<M>(d, nn);
+    const uint32_t gb = g.gbits(bgen != 0u), pb = g.gbits(eq == 0u);
+    const uint64_t Pm = pb, Gm = gb;
+    const uint64_t bin = (Pm + (Gm << 1)) ^ Pm;
+    sub_word<M>(d, (uint32_t)(bin >> g.t) & 1u);
+    const uint32_t borrow_out = (uint32_t)(bin >> G) & 1u;
+    const uint32_t ge = carry | (borrow_out ^ 1u);
+    const uint32_t msk = 0u - ge;
+#pragma unroll
+    for (int j = 0; j < M; ++j) c[j] = (d[j] & msk) | (c[j] & ~msk);
+    gsync();
+    sts<M>(OUT + g.t * M, c);
+    gsync();
+}
+
+// X <- X * Y * R^-1 mod N (or X^2 * R^-1 when square): X, Y, N, N' in shared memory.
+// red: 0 truncated (Alg. 6), 1 classical (Alg. 5).
+template <class S>
+MPG_DI void mont_mul(const Grp<S> &g, bool square, int red) {
+    constexpr int M = S::M, NP = S::NP;
+    uint32_t *T = g.T();
+    if (square) phase_sqr<S>(g, g.X(), g.Y(), T);   // Y and Q hold the block squares
+    else phase_mul<S>(g, g.X(), g.Y(), T);
+    // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0]
+    uint32_t nz_all = 0u, nz_low = 0u;
+    {
+        uint32_t x[M];
+        lds<M>(x, T + g.t * M);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            nz_all |= x[j];
+            if (g.t * M + j < NP - 1) nz_low |= x[j];
+        }
+    }
+    const uint32_t c_add = g.gbits(nz_all != 0u) ? 1u : 0u;
+    const uint32_t low_zero = g.gbits(nz_low != 0u) ? 0u : 1u;
+    phase_mullo<S>(g, T, g.NI(), g.Q());
+    if (red == 0) {
+        const uint32_t carry = phase_mulhi<S>(g, g.Q(), g.N(), T, c_add, low_zero, g.X());
+        cond_sub<S>(g, g.X(), carry, g.N(), g.X());
+    } else {
+        const uint32_t carry = phase_fma<S>(g, g.Q(), g.N(), T);
+        cond_sub<S>(g, T + NP, carry, g.N(), g.X());
+    }
+}
+
+}  // namespace mpg

@@ -1,0 +1,330 @@
+// Batched kernels built on the group arithmetic of mp_group.cuh, templated on the
+// group shape (G threads x M words per instance). Each shape is instantiated in
+// its own translation unit (mp_shape_*.cu) and exposed through a ShapeOps table.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include "mp_group.cuh"
+
+namespace mpg {
+
+enum { LAYOUT_IM = 0, LAYOUT_IL = 1 };
+
+// word i of instance k in an array of `words` words per instance
+MPG_DI size_t widx(int layout, size_t k, int i, int words, size_t batch) {
+    return layout == LAYOUT_IM ? k * (size_t)words + (size_t)i
+                               : (((size_t)(i >> 2) * batch + k) << 2) + (size_t)(i & 3);
+}
+
+// x[j] = word (w0 + j) of instance k, zero beyond `words` or for an invalid instance
+template <int M>
+MPG_DI void gload(uint32_t (&x)[M], const uint32_t *p, int layout, size_t k, bool valid, int w0,
+                  int words, size_t batch) {
+    if constexpr (M % 4 == 0) {
+        if (layout == LAYOUT_IL && (w0 & 3) == 0) {
+#pragma unroll
+            for (int c = 0; c < M / 4; ++c) {
+                const int i = w0 + 4 * c;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (valid && i < words) v = reinterpret_cast<const uint4 *>(p)[(size_t)(i >> 2) * batch + k];
+                x[4 * c] = v.x;
+                x[4 * c + 1] = (i + 1 < words) ? v.y : 0u;
+                x[4 * c + 2] = (i + 2 < words) ? v.z : 0u;
+                x[4 * c + 3] = (i + 3 < words) ? v.w : 0u;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int i = w0 + j;
+        x[j] = (valid && i < words) ? p[widx(layout, k, i, words, batch)] : 0u;
+    }
+}
+
+template <int M>
+MPG_DI void gstore(uint32_t *p, const uint32_t (&x)[M], int layout, size_t k, bool valid, int w0, int words,
+                   size_t batch) {
+    if (!valid) return;
+    if constexpr (M % 4 == 0) {
+        if (layout == LAYOUT_IL && (w0 & 3) == 0) {
+#pragma unroll
+            for (int c = 0; c < M / 4; ++c) {
+                const int i = w0 + 4 * c;
+                if (i + 3 < words) {
+                    reinterpret_cast<uint4 *>(p)[(size_t)(i >> 2) * batch + k] =
+                        make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (i + r < words) p[widx(layout, k, i + r, words, batch)] = x[4 * c + r];
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int i = w0 + j;
+        if (i < words) p[widx(layout, k, i, words, batch)] = x[j];
+    }
+}
+
+struct KArgs {
+    uint32_t *out;
+    const uint32_t *a;
+    const uint32_t *b;
+    const uint32_t *e;       // exponents (API layout, ne words)
+    // context arrays: interleaved layout, NP words per instance
+    const uint32_t *N;
+    const uint32_t *NI;
+    const uint32_t *R1;
+    const uint32_t *R2;
+    const uint32_t *K;
+    uint32_t *table;         // window tables: [entry][NP/4][batch] uint4
+    size_t batch;
+    int n;                   // API words per value
+    int layout;              // API layout
+    int ebits, ne, window, red, square, correct;
+};
+
+template <class S>
+MPG_DI Grp<S> make_group(uint32_t *smem) {
+    Grp<S> g;
+    const int gi = threadIdx.x / S::G;
+    g.sm = smem + gi * S::WORDS;
+    g.t = threadIdx.x % S::G;
+    g.gbase = (threadIdx.x & 31) & ~(S::G - 1);
+    return g;
+}
+
+template <class S>
+MPG_DI void init_zero_block(const Grp<S> &g) {
+    if (g.t == 0) {
+#pragma unroll
+        for (int j = 0; j < S::M; ++j) g.Z()[j] = 0u;
+    }
+}
+
+// load M words per thread of an API operand into shared memory
+template <class S>
+MPG_DI void load_api(const Grp<S> &g, uint32_t *dst, const uint32_t *src, const KArgs &A, size_t k, bool valid) {
+    uint32_t x[S::M];
+    gload<S::M>(x, src, A.layout, k, valid, g.t * S::M, A.n, A.batch);
+    sts<S::M>(dst + g.t * S::M, x);
+}
+
+template <class S>
+MPG_DI void load_ctx(const Grp<S> &g, uint32_t *dst, const uint32_t *src, const KArgs &A, size_t k, bool valid) {
+    uint32_t x[S::M];
+    gload<S::M>(x, src, LAYOUT_IL, k, valid, g.t * S::M, S::NP, A.batch);
+    sts<S::M>(dst + g.t * S::M, x);
+}
+
+// ------------------------------------------------------------------ mp_mul / mp_sqr
+
+template <class S, int TPB>
+__global__ void __launch_bounds__(TPB) k_mul(KArgs A) {
+    extern __shared__ uint4 smem4[];
+    Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
+    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    const bool valid = k < A.batch;
+    init_zero_block<S>(g);
+    load_api<S>(g, g.X(), A.a, A, k, valid);
+    if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
+    gsync();
+    if (A.square) phase_sqr<S>(g, g.X(), g.Y(), g.T());
+    else phase_mul<S>(g, g.X(), g.Y(), g.T());
+    // store 2n words
+    uint32_t x[2 * S::M];
+    lds<2 * S::M>(x, g.T() + 2 * g.t * S::M);
+    gstore<2 * S::M>(A.out, x, A.layout, k, valid, 2 * g.t * S::M, 2 * A.n, A.batch);
+}
+
+// ------------------------------------------------------------------ mont_mul / mont_sqr
+
+template <class S, int TPB>
+__global__ void __launch_bounds__(TPB) k_mont(KArgs A) {
+    extern __shared__ uint4 smem4[];
+    Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
+    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    const bool valid = k < A.batch;
+    init_zero_block<S>(g);
+    load_ctx<S>(g, g.N(), A.N, A, k, valid);
+    load_ctx<S>(g, g.NI(), A.NI, A, k, valid);
+    load_api<S>(g, g.X(), A.a, A, k, valid);
+    if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
+    gsync();
+    mont_mul<S>(g, A.square != 0, A.red);
+    if (A.correct) {   // internal radix W^NP differs from the API radix W^n: multiply by W^(2NP-n) mod N
+        load_ctx<S>(g, g.Y(), A.K, A, k, valid);
+        gsync();
+        mont_mul<S>(g, false, A.red);
+    }
+    uint32_t x[S::M];
+    lds<S::M>(x, g.X() + g.t * S::M);
+    gstore<S::M>(A.out, x, A.layout, k, valid, g.t * S::M, A.n, A.batch);
+}
+
+// ------------------------------------------------------------------ modexp
+
+template <class S>
+MPG_DI size_t tidx4(int e, int chunk, size_t k, size_t batch) {
+    return ((size_t)e * (S::NP / 4) + (size_t)chunk) * batch + k;
+}
+
+// constant-time window value b: bits [pos, pos+w) of the exponent, zero at or above ebits
+MPG_DI uint32_t window_bits(const KArgs &A, size_t k, bool valid, int pos, int w) {
+    if (!valid) return 0u;
+    const int wi = pos >> 5, sh = pos & 31;
+    const uint32_t lo = (wi < A.ne) ? A.e[widx(A.layout, k, wi, A.ne, A.batch)] : 0u;
+    const uint32_t hi = (wi + 1 < A.ne) ? A.e[widx(A.layout, k, wi + 1, A.ne, A.batch)] : 0u;
+    uint32_t v = (uint32_t)((((uint64_t)hi << 32) | lo) >> sh) & ((1u << w) - 1u);
+    const int keep = A.ebits - pos;   // public
+    if (keep < w) v &= (1u << keep) - 1u;
+    return v;
+}
+
+template <class S, int TPB>
+__global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
+    constexpr int M = S::M, NP = S::NP;
+    extern __shared__ uint4 smem4[];
+    Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
+    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    const bool valid = k < A.batch;
+    const int w = A.window;
+    const int E = 1 << w;
+    const size_t batch = A.batch;
+    uint4 *tab = reinterpret_cast<uint4 *>(A.table);
+    static_assert(M % 4 == 0 || M % 2 == 0, "");
+
+    auto put = [&](int e, const uint32_t *src) {
+        uint32_t x[M];
+        lds<M>(x, src + g.t * M);
+        if (!valid) return;
+        if constexpr (M % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < M / 4; ++c)
+                tab[tidx4<S>(e, g.t * (M / 4) + c, k, batch)] =
+                    make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const int i = g.t * M + j;
+                A.table[tidx4<S>(e, i >> 2, k, batch) * 4 + (i & 3)] = x[j];
+            }
+        }
+    };
+
+    init_zero_block<S>(g);
+    load_ctx<S>(g, g.N(), A.N, A, k, valid);
+    load_ctx<S>(g, g.NI(), A.NI, A, k, valid);
+    load_api<S>(g, g.X(), A.a, A, k, valid);
+    load_ctx<S>(g, g.Y(), A.R2, A, k, valid);
+    gsync();
+    mont_mul<S>(g, false, A.red);                 // X = a*R mod N = G[1]
+    put(1, g.X());
+    {   // Y = G[1]; G[0] = R mod N
+        uint32_t x[M];
+        lds<M>(x, g.X() + g.t * M);
+        sts<M>(g.Y() + g.t * M, x);
+        load_ctx<S>(g, g.X(), A.R1, A, k, valid);
+        gsync();
+        put(0, g.X());
+        lds<M>(x, g.Y() + g.t * M);
+        sts<M>(g.X() + g.t * M, x);
+        gsync();
+    }
+    for (int e = 2; e < E; ++e) {                 // G[e] = G[e-1] * G[1]
+        mont_mul<S>(g, false, A.red);
+        put(e, g.X());
+    }
+    load_ctx<S>(g, g.X(), A.R1, A, k, valid);     // Y_acc = 1 in Montgomery form
+    gsync();
+    const int windows = (A.ebits + w - 1) / w;
+    for (int win = windows - 1; win >= 0; --win) {
+        for (int s = 0; s < w; ++s) mont_mul<S>(g, true, A.red);
+        const uint32_t bsel = window_bits(A, k, valid, win * w, w);
+        // masked scan of the whole table: every entry is read, one is kept
+        uint32_t acc[M];
+        zero<M>(acc);
+        for (int e = 0; e < E; ++e) {
+            const uint32_t m = mask_if_equal((uint32_t)e, bsel);
+            uint32_t x[M];
+            if constexpr (M % 4 == 0) {
+#pragma unroll
+                for (int c = 0; c < M / 4; ++c) {
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, k, batch)];
+                    x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const int i = g.t * M + j;
+                    x[j] = valid ? A.table[tidx4<S>(e, i >> 2, k, batch) * 4 + (i & 3)] : 0u;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
+        }
+        sts<M>(g.Y() + g.t * M, acc);
+        gsync();
+        mont_mul<S>(g, false, A.red);
+    }
+    {   // leave the Montgomery domain: X * 1 * R^-1
+        uint32_t x[M];
+        zero<M>(x);
+        if (g.t == 0) x[0] = 1u;
+        sts<M>(g.Y() + g.t * M, x);
+        gsync();
+        mont_mul<S>(g, false, A.red);
+    }
+    uint32_t x[M];
+    lds<M>(x, g.X() + g.t * M);
+    gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
+    (void)NP;
+}
+
+// ------------------------------------------------------------------ per-shape launch table
+
+struct ShapeOps {
+    int G, M, NP, tpb;
+    size_t smem_bytes;
+    cudaError_t (*mul)(const KArgs &, cudaStream_t);
+    cudaError_t (*mont)(const KArgs &, cudaStream_t);
+    cudaError_t (*modexp)(const KArgs &, cudaStream_t);
+};
+
+// KIND tells the kernels of one shape apart, so that each gets its own attribute call
+template <class S, int TPB, int KIND, class F>
+static cudaError_t launch_k(F kern, const KArgs &A, cudaStream_t st) {
+    constexpr int GPB = TPB / S::G;
+    const size_t smem = (size_t)GPB * S::WORDS * 4;
+    static bool attr_set = false;   // one attribute call per kernel and process
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const size_t blocks = (A.batch + GPB - 1) / GPB;
+    kern<<<(unsigned)blocks, TPB, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <class S, int TPB>
+struct ShapeImpl {
+    static cudaError_t mul(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 0>(k_mul<S, TPB>, A, st); }
+    static cudaError_t mont(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 1>(k_mont<S, TPB>, A, st); }
+    static cudaError_t modexp(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 2>(k_modexp<S, TPB>, A, st); }
+    static ShapeOps ops() {
+        return ShapeOps{S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont, &modexp};
+    }
+};
+
+}  // namespace mpg
+
+#define MPG_DEFINE_SHAPE(G, M, TPB)                                              \
+    namespace mpg {                                                              \
+    ShapeOps shape_ops_##G##_##M() { return ShapeImpl<Shape<G, M>, TPB>::ops(); } \
+    }

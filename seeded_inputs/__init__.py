@@ -170,19 +170,31 @@ def random_prime(rng: np.random.Generator, bits: int, rounds: int = 24) -> int:
                 return x
 
 
-def prime_pool(seed: int, workload: str, count: int, bits: int) -> list[int]:
-    rng = stream(seed, workload, "prime")
-    return [random_prime(rng, bits) for _ in range(count)]
+def _pool_prime(args):
+    seed, workload, i, bits = args
+    return random_prime(stream(seed, workload, "prime", i), bits)
 
 
-def rsa_moduli(seed: int, workload: str, batch: int, bits: int, pool_size: int | None = None) -> np.ndarray:
+def prime_pool(seed: int, workload: str, count: int, bits: int, procs: int = 0) -> list[int]:
+    """``count`` primes; prime i comes from its own stream, so the pool is the same
+    whether it is generated serially or by a (spawned) process pool."""
+    jobs = [(seed, workload, i, bits) for i in range(count)]
+    if procs and procs > 1 and count > 8:
+        import multiprocessing as mproc
+        with mproc.get_context("spawn").Pool(procs) as pool:
+            return pool.map(_pool_prime, jobs, chunksize=max(1, count // (4 * procs)))
+    return [_pool_prime(j) for j in jobs]
+
+
+def rsa_moduli(seed: int, workload: str, batch: int, bits: int, pool_size: int | None = None,
+               procs: int = 0) -> np.ndarray:
     """``batch`` products p*q of distinct primes of bits/2 bits (top two bits set),
     drawn as distinct pairs from a seeded pool of primes; each product has exactly
     ``bits`` bits. The pool is the smallest size whose pair count covers ``batch``
     (at least 2), so the cost of prime generation stays bounded."""
     if pool_size is None:
         pool_size = max(2, int(math.ceil((1 + math.sqrt(1 + 8 * batch)) / 2)))
-    primes = prime_pool(seed, workload, pool_size, bits // 2)
+    primes = prime_pool(seed, workload, pool_size, bits // 2, procs)
     rng = stream(seed, workload, "pool")
     pairs = set()
     out = []
@@ -221,14 +233,14 @@ class Batch:
 
 
 def make_batch(seed: int, workload: str, batch: int, bits: int, ebits: int | None = None,
-               rsa_fraction: float = 0.0, sub: int = 0) -> Batch:
+               rsa_fraction: float = 0.0, sub: int = 0, procs: int = 0) -> Batch:
     """Random odd moduli (a fraction of them RSA-like products), bases a, b < N and
     ``ebits``-bit exponents (default: full length, ``ebits = bits``)."""
     ebits = bits if ebits is None else ebits
     N = random_odd_moduli(stream(seed, workload, "modulus", sub), batch, bits)
     n_rsa = int(round(batch * rsa_fraction))
     if n_rsa:
-        N[batch - n_rsa:] = rsa_moduli(seed, workload, n_rsa, bits)
+        N[batch - n_rsa:] = rsa_moduli(seed, workload, n_rsa, bits, procs=procs)
     rb = stream(seed, workload, "base", sub)
     a = uniform_below(rb, N, bits)
     b = uniform_below(rb, N, bits)
@@ -242,9 +254,9 @@ def plain_small(seed: int = 0) -> Batch:
     return make_batch(seed, "plain_small", 8, 1024)
 
 
-def batch_2048(seed: int = 0, batch: int = 65536) -> Batch:
+def batch_2048(seed: int = 0, batch: int = 65536, procs: int = 0) -> Batch:
     """2048-bit moduli, half random odd, half products of two 1024-bit primes."""
-    return make_batch(seed, "batch_2048", batch, 2048, rsa_fraction=0.5)
+    return make_batch(seed, "batch_2048", batch, 2048, rsa_fraction=0.5, procs=procs)
 
 
 def batch_4096(seed: int = 0, batch: int = 16384, bits: int = 4096) -> Batch:

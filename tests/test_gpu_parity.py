@@ -1,0 +1,254 @@
+"""GPU parity: every entry point through the C ABI, compared word for word with the
+CPU oracle on the same seeded inputs (integer results: bit-exact, tolerance 0)."""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2410_18129_gb300 as mp
+    assert torch.cuda.is_available()
+    return mp
+
+
+IM, IL = 0, 1
+
+
+def dev(mp, x, layout):
+    """[batch, w] numpy -> device tensor in `layout`."""
+    flat = x.reshape(-1) if layout == IM else mp.interleave(x)
+    return mp.to_device(flat)
+
+
+def host(mp, t, batch, w, layout):
+    a = mp.to_host(t)
+    return a.reshape(batch, w) if layout == IM else mp.deinterleave(a, batch, w)
+
+
+def out_tensor(mp, batch, w, layout):
+    return torch.zeros(mp.array_words(layout, batch, w), dtype=torch.int32, device="cuda")
+
+
+def assert_equal(got, want, what):
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, f"{what}: {bad.size} instances differ, first {bad[:8]}"
+
+
+SIZES = [64, 100, 256, 512, 1000, 1024, 2048, 3072, 4096, 4108, 4154]
+
+
+# ------------------------------------------------------------------ products
+
+@pytest.mark.parametrize("bits", SIZES)
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_mp_mul_sqr(mp, bits, layout):
+    batch = 37 if bits > 3000 else 301          # ragged: several blocks plus a partial one
+    b = si.make_batch(0, "test", batch, bits, ebits=1, sub=bits)
+    n = b.n
+    a_np = si.random_bits(si.stream(0, "test", "other", bits), batch, bits)
+    a_np[0] = 0xFFFFFFFF                         # the largest bits-bit value
+    if bits % 32:
+        a_np[0, n - 1] = (1 << (bits % 32)) - 1
+    a_np[1] = 0
+    A = dev(mp, a_np, layout)
+    B = dev(mp, b.b, layout)
+    C = out_tensor(mp, batch, 2 * n, layout)
+    mp.mp_mul(C, A, B, batch, bits, layout)
+    assert_equal(host(mp, C, batch, 2 * n, layout), oracle.mul(a_np, b.b), f"mp_mul {bits}")
+    mp.mp_sqr(C, A, batch, bits, layout)
+    assert_equal(host(mp, C, batch, 2 * n, layout), oracle.sqr(a_np), f"mp_sqr {bits}")
+
+
+def test_mp_mul_single_instance_and_tiny(mp):
+    for bits in (32, 33, 64):
+        x = si.random_bits(si.stream(0, "test", "other", 7), 1, bits)
+        y = si.random_bits(si.stream(0, "test", "other", 8), 1, bits)
+        n = x.shape[1]
+        C = out_tensor(mp, 1, 2 * n, IM)
+        mp.mp_mul(C, dev(mp, x, IM), dev(mp, y, IM), 1, bits, IM)
+        assert_equal(host(mp, C, 1, 2 * n, IM), oracle.mul(x, y), "tiny mul")
+
+
+# ------------------------------------------------------------------ Montgomery context
+
+@pytest.mark.parametrize("bits", [64, 100, 1024, 2048, 4108])
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_ctx_constants(mp, bits, layout):
+    batch = 45
+    N = si.random_odd_moduli(si.stream(0, "test", "modulus", bits), batch, bits)
+    N[0] = 0xFFFFFFFF
+    if bits % 32:
+        N[0, -1] &= np.uint32((1 << (bits % 32)) - 1)
+    ctx = mp.MontCtx(dev(mp, N, layout), batch, bits, layout)
+    Np, r1, r2 = oracle.ctx(N)
+    n = N.shape[1]
+    assert_equal(host(mp, ctx.export(0), batch, n, layout), Np, "N'")
+    assert_equal(host(mp, ctx.export(1), batch, n, layout), r1, "R mod N")
+    assert_equal(host(mp, ctx.export(2), batch, n, layout), r2, "R^2 mod N")
+    assert_equal(host(mp, ctx.export(3), batch, n, layout), N, "N")
+    ctx.free()
+
+
+def test_ctx_even_modulus_reports_first_index(mp):
+    N = si.random_odd_moduli(si.stream(0, "test", "modulus", 1), 10, 1024)
+    N[6, 0] &= np.uint32(0xFFFFFFFE)
+    N[8, 0] &= np.uint32(0xFFFFFFFE)
+    with pytest.raises(mp.MpError) as e:
+        mp.MontCtx(dev(mp, N, IM), 10, 1024, IM)
+    assert e.value.status == -3 and e.value.bad_index == 6
+
+
+# ------------------------------------------------------------------ Montgomery products
+
+@pytest.mark.parametrize("bits", [64, 100, 512, 1000, 1024, 2048, 3072, 4096, 4108, 4154])
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_mont_mul_sqr(mp, bits, layout):
+    batch = 29 if bits > 3000 else 203
+    b = si.make_batch(0, "test", batch, bits, ebits=1, sub=1000 + bits)
+    b.a[0] = 0
+    b.a[1] = b.N[1] - np.array([1] + [0] * (b.n - 1), np.uint32)   # N-1 (N odd, no borrow)
+    b.b[1] = b.a[1]
+    n = b.n
+    ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
+    A, B = dev(mp, b.a, layout), dev(mp, b.b, layout)
+    C = out_tensor(mp, batch, n, layout)
+    want_mul = oracle.mont_def(b.a, b.b, b.N)
+    want_sqr = oracle.mont_def(b.a, b.a, b.N)
+    for red in (mp.RED_TRUNCATED, mp.RED_FULL):
+        mp.mont_mul(C, A, B, ctx, red)
+        assert_equal(host(mp, C, batch, n, layout), want_mul, f"mont_mul {bits} red={red}")
+        mp.mont_sqr(C, A, ctx, red)
+        assert_equal(host(mp, C, batch, n, layout), want_sqr, f"mont_sqr {bits} red={red}")
+    ctx.free()
+
+
+def test_mont_mul_in_place(mp):
+    bits, batch = 2048, 64
+    b = si.make_batch(0, "test", batch, bits, ebits=1, sub=77)
+    ctx = mp.MontCtx(dev(mp, b.N, IL), batch, bits, IL)
+    A, B = dev(mp, b.a, IL), dev(mp, b.b, IL)
+    mp.mont_mul(A, A, B, ctx)
+    assert_equal(host(mp, A, batch, b.n, IL), oracle.mont_def(b.a, b.b, b.N), "in place")
+
+
+def test_mont_special_moduli(mp):
+    """N = 2^t - 1 and N = 2^(t-1) + 1 with the extreme operands."""
+    bits = 2048
+    n = 64
+    Ns = [2 ** bits - 1, 2 ** (bits - 1) + 1]
+    rows = []
+    for N in Ns:
+        for a, bb in ((0, 0), (1, 1), (N - 1, N - 1), (N - 1, 1), (N // 2, N // 3)):
+            rows.append((N, a, bb))
+    N = si.from_ints([r[0] for r in rows], n)
+    a = si.from_ints([r[1] for r in rows], n)
+    bb = si.from_ints([r[2] for r in rows], n)
+    B = len(rows)
+    ctx = mp.MontCtx(dev(mp, N, IM), B, bits, IM)
+    C = out_tensor(mp, B, n, IM)
+    for red in (0, 1):
+        mp.mont_mul(C, dev(mp, a, IM), dev(mp, bb, IM), ctx, red)
+        assert_equal(host(mp, C, B, n, IM), oracle.mont_def(a, bb, N), f"special red={red}")
+
+
+# ------------------------------------------------------------------ exponentiation
+
+@pytest.mark.parametrize("bits,batch,window", [(1024, 8, 5), (1024, 67, 4), (2048, 40, 5), (512, 100, 3),
+                                               (100, 50, 2), (4096, 6, 6), (3072, 6, 5), (4108, 3, 5)])
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_modexp(mp, bits, batch, window, layout):
+    b = si.make_batch(0, "test", batch, bits, sub=2000 + bits)
+    ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
+    Y = out_tensor(mp, batch, b.n, layout)
+    want = oracle.modexp(b.a, b.e, b.ebits, b.N)
+    for red in (0, 1):
+        mp.modexp_consttime(Y, dev(mp, b.a, layout), dev(mp, b.e, layout), b.ebits, ctx, window, red)
+        assert_equal(host(mp, Y, batch, b.n, layout), want, f"modexp {bits} w={window} red={red}")
+
+
+def test_modexp_window_independence_and_workspace(mp):
+    bits, batch = 1024, 33
+    b = si.make_batch(0, "test", batch, bits, sub=31)
+    ctx = mp.MontCtx(dev(mp, b.N, IL), batch, bits, IL)
+    want = oracle.modexp(b.a, b.e, b.ebits, b.N)
+    A, E = dev(mp, b.a, IL), dev(mp, b.e, IL)
+    for w in range(1, 7):
+        ws = torch.empty(mp.modexp_workspace_bytes(batch, bits, w) // 4, dtype=torch.int32, device="cuda")
+        Y = out_tensor(mp, batch, b.n, IL)
+        mp.modexp_consttime(Y, A, E, bits, ctx, w, workspace=ws)
+        assert_equal(host(mp, Y, batch, b.n, IL), want, f"w={w}")
+    small = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(mp.MpError):
+        mp.modexp_consttime(Y, A, E, bits, ctx, 5, workspace=small)
+
+
+def test_modexp_special_cases(mp):
+    bits = 1024
+    n = 32
+    N1 = si.to_int(si.random_odd_moduli(si.stream(0, "test", "modulus", 5), 1, bits)[0])
+    rows = []
+    for N in (N1, 2 ** bits - 1, 2 ** (bits - 1) + 1):
+        for a in (0, 1, N - 1, 2):
+            for e in (0, 1, 2, 2 ** bits - 1, 2 ** (bits - 1)):
+                rows.append((N, a, e))
+    B = len(rows)
+    N = si.from_ints([r[0] for r in rows], n)
+    a = si.from_ints([r[1] for r in rows], n)
+    e = si.from_ints([r[2] for r in rows], n)
+    ctx = mp.MontCtx(dev(mp, N, IM), B, bits, IM)
+    Y = out_tensor(mp, B, n, IM)
+    mp.modexp_consttime(Y, dev(mp, a, IM), dev(mp, e, IM), bits, ctx, 5)
+    got = host(mp, Y, B, n, IM)
+    for k, (Nk, ak, ek) in enumerate(rows):
+        assert si.to_int(got[k]) == pow(ak, ek, Nk), (k, hex(Nk)[:10], ak == Nk - 1, ek)
+    # exponent of 0 declared bits: every result is 1 mod N
+    mp.modexp_consttime(Y, dev(mp, a, IM), dev(mp, e, IM), 0, ctx, 5)
+    assert all(si.to_int(v) == 1 for v in host(mp, Y, B, n, IM))
+
+
+def test_modexp_short_exponents(mp):
+    bits, batch = 2048, 20
+    for ebits in (1, 31, 32, 33, 77, 160):
+        b = si.make_batch(0, "test", batch, bits, ebits=ebits, sub=ebits)
+        ctx = mp.MontCtx(dev(mp, b.N, IL), batch, bits, IL)
+        Y = out_tensor(mp, batch, b.n, IL)
+        mp.modexp_consttime(Y, dev(mp, b.a, IL), dev(mp, b.e, IL), ebits, ctx, 5)
+        assert_equal(host(mp, Y, batch, b.n, IL), oracle.modexp(b.a, b.e, ebits, b.N), f"ebits={ebits}")
+
+
+def test_fermat_on_generated_primes(mp):
+    r = si.stream(0, "test", "prime", 3)
+    primes = [si.random_prime(r, 1024) for _ in range(4)]
+    n = 32
+    N = si.from_ints(primes * 4, n)
+    a = si.uniform_below(r, N, 1024)
+    e = si.from_ints([p - 1 for p in primes * 4], n)
+    B = N.shape[0]
+    ctx = mp.MontCtx(dev(mp, N, IM), B, 1024, IM)
+    Y = out_tensor(mp, B, n, IM)
+    mp.modexp_consttime(Y, dev(mp, a, IM), dev(mp, e, IM), 1024, ctx, 5)
+    assert all(si.to_int(v) == 1 for v in host(mp, Y, B, n, IM))
+
+
+# ------------------------------------------------------------------ layout conversion
+
+@pytest.mark.parametrize("w", [1, 3, 4, 64, 129])
+def test_convert_round_trip(mp, w):
+    batch = 77
+    x = si.random_bits(si.stream(0, "test", "other", w), batch, 32 * w)
+    src = dev(mp, x, IM)
+    mid = out_tensor(mp, batch, w, IL)
+    back = out_tensor(mp, batch, w, IM)
+    mp.mp_convert(mid, IL, src, IM, batch, w)
+    got, want = mp.to_host(mid), mp.interleave(x)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"{bad.size} words differ, first at {bad[:6]}: got {got[bad[:6]]} want {want[bad[:6]]}"
+    mp.mp_convert(back, IM, mid, IL, batch, w)
+    assert (mp.to_host(back).reshape(batch, w) == x).all()
