@@ -130,6 +130,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the modexp steps only (no comparison runs, no e2e, no CPU baseline): for profiling")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,6 +228,14 @@ def main():
     clocks = clk.summary()
     ms_step = ms / args.steps
     value = world * B / (ms_step / 1e3)
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "modexp/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                              "quick": True, "batch_per_gpu": B, "clocks": clocks}))
+        ctx.free()
+        return
 
     # classical reduction for comparison
     for _ in range(1):
