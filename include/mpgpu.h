@@ -147,6 +147,31 @@ int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uin
                      void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * modexp_consttime without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory on the
+ * call path, e.g. a service that reserved its whole memory budget up front, code
+ * that cannot afford the device-wide synchronisation and unpredictable latency of
+ * cudaMalloc/cudaFree, or a host process whose device memory belongs to another
+ * allocator. Same arguments and results as modexp_consttime minus the workspace:
+ * the window tables go to one static device array of MPGPU_NOALLOC_SCRATCH_BYTES
+ * bytes inside the library (every GPU that loads the library holds it until the
+ * process exits). The call allocates nothing; the context still comes from
+ * mont_ctx_init, done beforehand.
+ *   - Limit: modexp_workspace_bytes(batch, bits, window) must not exceed
+ *     MPGPU_NOALLOC_SCRATCH_BYTES (16 MiB: e.g. 2048 instances of 2048 bits at w=5,
+ *     512 of 4096 bits at w=6); larger batches return MP_ERR_SIZE before any work.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the array, which keeps the last call's contents (each call
+ *     writes every table entry before reading it). Calls that overlap on the GPU
+ *     (concurrent streams or host threads) race on it: serialise them.
+ */
+#define MPGPU_NOALLOC_SCRATCH_BYTES (16u << 20)
+int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
+                             const mont_ctx *ctx, uint32_t window, mp_red red, mp_algo algo, void *stream);
+
+/*
  * Measurement helper (no counterpart in the paper; it sets the roofline): runs one
  * block of 1024 threads per SM executing `iters` rounds of an integer instruction
  * mix and returns the issued rate per SM per clock (lanes x instructions / cycles,

@@ -45,6 +45,7 @@ _SIG = {
     "modexp_workspace_bytes": ([_sz, _u32, _u32], _sz),
     "modexp_consttime": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp, _sz, _vp], _i),
     "mp_bench_imad": ([_i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp], _i),
+    "modexp_consttime_noalloc": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp], _i),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -170,6 +171,18 @@ def modexp_consttime(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_lib.modexp_consttime(_ptr(y), _ptr(base), _ptr(exp), exp_bits, ctx.handle, window, red, algo,
                                  _ptr(workspace), ws_bytes, _stream()), "modexp_consttime")
+    return y
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def modexp_consttime_noalloc(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,
+                             red: int = RED_TRUNCATED, algo: int = ALGO_AUTO):
+    """modexp_consttime with its window tables in the library's fixed device array
+    (no allocation; at most NOALLOC_SCRATCH_BYTES of tables; concurrent calls race)."""
+    _check(_lib.modexp_consttime_noalloc(_ptr(y), _ptr(base), _ptr(exp), exp_bits, ctx.handle, window, red,
+                                         algo, _stream()), "modexp_consttime_noalloc")
     return y
 
 

@@ -404,3 +404,58 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     }
     return rc;
 }
+
+// ------------------------------------------------------------------ exponentiation without allocation
+//
+// Window tables of modexp_consttime_noalloc live in this fixed device array
+// instead of a caller workspace or a stream-ordered allocation. It is part of the
+// library's device image, so every GPU that loads the library holds these bytes
+// until the process exits. All calls share it and it keeps what the last call
+// wrote; the exponentiation writes every table entry before reading it, so
+// nothing needs clearing between calls. Two calls that overlap on the GPU (two
+// streams, or two host threads) race on it.
+static __device__ __align__(256) uint4 g_noalloc_tables[MPGPU_NOALLOC_SCRATCH_BYTES / 16];
+
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static uint32_t *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+
+// Device address of the array on the current device. In host code the array's
+// name only stands for the device symbol, so the address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+static int noalloc_tables(uint32_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MP_ERR_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_tables) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MP_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = reinterpret_cast<uint32_t *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return MP_OK;
+}
+
+extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
+                                        const mont_ctx *c, uint32_t window, mp_red red, mp_algo algo,
+                                        void *stream) {
+    if (!y || !base || !c || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
+    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    if (window == 0) window = tuned_window(c->bits);
+    if (window > 6) return MP_ERR_SIZE;
+    if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp))))
+        return MP_ERR_ALIGN;
+    if (modexp_workspace_bytes(c->batch, c->bits, window) > (size_t)MPGPU_NOALLOC_SCRATCH_BYTES) return MP_ERR_SIZE;
+    uint32_t *tables = nullptr;
+    int rc = noalloc_tables(&tables);
+    if (rc != MP_OK) return rc;
+    KArgs A{};
+    fill_ctx_args(A, c);
+    A.out = y; A.a = base; A.e = exp; A.table = tables;
+    A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
+    A.red = (int)red;
+    return cuda_status(c->shape->modexp(A, S(stream)));
+}
