@@ -13,6 +13,10 @@ using namespace mpg;
 // mode 1: independent high-half multiply-adds (mad.hi.u32)
 // mode 2: the library's 8x8 block product (mad.lo.cc / madc.hi.cc carry chains), 128 IMAD per call
 // mode 3: 32-bit add-with-carry chains (add.cc / addc.cc), 8 words
+// mode 4: independent mad.wide.u32 (32x32+64 -> 64), counted as two multiply-adds
+// mode 5: 8x8 block product from mad.wide.u32 plus 64-bit carry adds
+// mode 6: two independent 8x8 carry-chain block products per iteration
+// mode 7: mode 2 with 256 active threads per SM
 __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
     uint32_t a[8], b[8];
 #pragma unroll
@@ -42,13 +46,73 @@ __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long
 #pragma unroll
             for (int i = 0; i < 8; ++i) { a[i] ^= P[i]; b[i] += P[8 + i]; }
         }
-    } else {
+    } else if (mode == 3) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
                 add_cc(a[0], b[0]);
 #pragma unroll
                 for (int i = 1; i < 8; ++i) addc_cc(a[i], b[i]);
+            }
+        }
+    } else if (mode == 4) {
+        // independent 32x32+64 -> 64 multiply-adds (mad.wide.u32), 8 chains; counted as 2 (lo + hi)
+        uint64_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = ((uint64_t)a[i] << 32) | b[i];
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[i]) : "r"(b[i]), "r"(a[(i + 1) & 7]));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] ^= (uint32_t)w[i] ^ (uint32_t)(w[i] >> 32);
+    } else if (mode == 5) {
+        // 8x8 block product by operand scanning with mad.wide.u32: t = a_i*b_j + r + carry
+        uint32_t P[16];
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) P[j] = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                uint32_t carry = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint64_t t;
+                    asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(t) : "r"(a[i]), "r"(b[j]), "l"((uint64_t)P[i + j]));
+                    t += carry;
+                    P[i + j] = (uint32_t)t;
+                    carry = (uint32_t)(t >> 32);
+                }
+                P[i + 8] = carry;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { a[i] ^= P[i]; b[i] += P[8 + i]; }
+        }
+    } else if (mode == 6) {
+        // two independent 8x8 carry-chain block products per iteration (instruction-level parallelism)
+        uint32_t P[16], Q[16], c[8], d[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { c[i] = a[i] * 3u + 1u; d[i] = b[i] ^ 0x55555555u; }
+        for (int it = 0; it < iters; ++it) {
+            block_mul<8>(P, a, b);
+            block_mul<8>(Q, c, d);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { a[i] ^= P[i]; b[i] += P[8 + i]; c[i] ^= Q[i]; d[i] += Q[8 + i]; }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] ^= c[i] + d[i];
+    } else {
+        // mode 7: the 8x8 block product with 256 threads per SM (low occupancy)
+        uint32_t P[16];
+        if (threadIdx.x < 256) {
+            for (int it = 0; it < iters; ++it) {
+                block_mul<8>(P, a, b);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) { a[i] ^= P[i]; b[i] += P[8 + i]; }
             }
         }
     }
@@ -62,7 +126,7 @@ __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long
 }
 
 extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream) {
-    if (mode < 0 || mode > 3 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
+    if (mode < 0 || mode > 7 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MP_ERR_CUDA;
@@ -85,8 +149,11 @@ extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double
         cudaMemcpy(c.data(), cyc, (size_t)sms * 8, cudaMemcpyDeviceToHost);
         std::sort(c.begin(), c.end());
         const double med = (double)c[sms / 2];
-        const double per_thread = mode == 2 ? 128.0 * iters : mode == 3 ? 128.0 * iters : 128.0 * iters;
-        *per_clk_per_sm = per_thread * threads / med;
+        // multiply-adds per thread: every mode is sized to 128 per iteration (mode 6: 256),
+        // mode 7 runs on a quarter of the threads
+        const double per_thread = (mode == 6 ? 256.0 : 128.0) * iters;
+        const double active = mode == 7 ? 256.0 : (double)threads;
+        *per_clk_per_sm = per_thread * active / med;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (sm_mhz) *sm_mhz = (double)c[sms - 1] / (ms * 1e3);

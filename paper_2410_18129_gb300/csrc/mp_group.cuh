@@ -5,11 +5,12 @@
 // products, B = M/2 for the truncated halves). Output columns are cut into
 // slots of B words; every thread owns two slots chosen so that all threads do
 // the same number of block products (balanced even for the triangular low and
-// high halves), accumulates each slot in registers, and parks the raw slot
-// sums in shared memory. A carry-resolution pass then turns the overlapping
-// slot sums into words: each slot adds the spill of its predecessor, passes
-// on a small overflow word, and the remaining one-bit carries are resolved
-// for the whole group at once with a warp ballot (carry-lookahead).
+// high halves) and accumulates each slot in registers. When a slot is complete
+// its low B words go straight to the phase's output array and its spill (the
+// words above, B+2 of them) to a small shared area. A carry-resolution pass then
+// adds each predecessor's spill, passes a small overflow word to the successor
+// through a shuffle, and resolves the remaining one-bit carries for the whole
+// group at once with warp ballots (carry-lookahead).
 //
 // Montgomery product (Alg. 5 / Alg. 6 in 32-bit words, R = 2^(32*NP)):
 //   1. T = X*Y            (Alg. 1) or T = X^2 (Alg. 2)
@@ -35,15 +36,13 @@ struct Shape {
     static_assert(G >= 2 && G <= 16 && (G & (G - 1)) == 0, "G must be 2, 4, 8 or 16");
     static_assert(M >= 4 && M % 2 == 0, "M must be even and >= 4");
     // per-instance shared memory map (32-bit words)
-    static constexpr int OFF_X = 0;               // operand / result
-    static constexpr int OFF_Y = NP;              // operand (Y and Q together hold the squares of X)
-    static constexpr int OFF_Q = 2 * NP;          // q
-    static constexpr int OFF_N = 3 * NP;          // modulus
-    static constexpr int OFF_NI = 4 * NP;         // N' = (-N)^-1 mod R
-    static constexpr int OFF_T = 5 * NP;          // T (2*NP words)
-    static constexpr int OFF_P = 7 * NP;          // raw slot sums
-    static constexpr int OFF_OV = OFF_P + 2 * G * A1;   // overflow words (2 per slot)
-    static constexpr int OFF_Z = OFF_OV + 4 * G;        // M zero words
+    static constexpr int OFF_X = 0;               // operand / result; X and Y together hold the block squares
+    static constexpr int OFF_Y = NP;              // operand, then q
+    static constexpr int OFF_N = 2 * NP;          // modulus
+    static constexpr int OFF_NI = 3 * NP;         // N' = (-N)^-1 mod R
+    static constexpr int OFF_T = 4 * NP;          // T (2*NP words)
+    static constexpr int OFF_P = 6 * NP;          // slot spills: 2G slots of M+2 words
+    static constexpr int OFF_Z = OFF_P + 2 * G * (M + 2);   // M zero words
     static constexpr int WORDS_RAW = OFF_Z + M;
     static constexpr int WORDS = (WORDS_RAW + 3) & ~3;  // keep every instance 16-byte aligned
 };
@@ -56,12 +55,11 @@ struct Grp {
     int gbase;      // warp lane of thread 0 of the group
     MPG_DI uint32_t *X() const { return sm + S::OFF_X; }
     MPG_DI uint32_t *Y() const { return sm + S::OFF_Y; }
-    MPG_DI uint32_t *Q() const { return sm + S::OFF_Q; }
+    MPG_DI uint32_t *Q() const { return sm + S::OFF_Y; }   // q reuses Y once T is formed
     MPG_DI uint32_t *N() const { return sm + S::OFF_N; }
     MPG_DI uint32_t *NI() const { return sm + S::OFF_NI; }
     MPG_DI uint32_t *T() const { return sm + S::OFF_T; }
     MPG_DI uint32_t *P() const { return sm + S::OFF_P; }
-    MPG_DI uint32_t *OV() const { return sm + S::OFF_OV; }
     MPG_DI uint32_t *Z() const { return sm + S::OFF_Z; }
     // this group's bits of a warp ballot
     MPG_DI uint32_t gbits(bool pred) const {
@@ -144,51 +142,95 @@ MPG_DI uint64_t slot_mask(uint32_t bitsA, uint32_t bitsB) {
 }
 
 struct NoXform {
+    static constexpr bool active = false;
     template <int A>
     MPG_DI void operator()(int, uint32_t (&)[A]) const {}
 };
 
-// Turn the raw slot sums P[s] (A = 2B+2 words each, slot s covering output words
-// [s*B, s*B+B) and spilling into the next slots) into words OUT[s*B..s*B+B).
-// in0: B+2 words added below slot 0 (a carry coming from outside). xf may rewrite a
-// slot sum first (add an addend, double it ...). Returns the low word of everything
-// above the last slot (its own spill and overflow plus the resolved carry).
+// complete slot s: low B words to its output position, the rest to its spill area
+template <int B>
+MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
+    uint32_t lo[B], hi[B + 2];
+#pragma unroll
+    for (int j = 0; j < B; ++j) lo[j] = V[j];
+#pragma unroll
+    for (int j = 0; j < B + 2; ++j) hi[j] = V[B + j];
+    sts<B>(out_lo, lo);
+    sts<B + 2>(spill, hi);
+    zero<2 * B + 2>(V);
+}
+
+// overflow words of the predecessor slot, passed between lanes with shuffles
+template <int G, int PAT>
+MPG_DI void pred_overflow(int t, int gbase, const uint32_t (&ovA)[2], const uint32_t (&ovB)[2],
+                          uint32_t (&inA)[2], uint32_t (&inB)[2]) {
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+        const uint32_t up = __shfl_sync(0xffffffffu, ovA[w], gbase + (t > 0 ? t - 1 : 0));
+        inA[w] = t > 0 ? up : 0u;                                   // slot t <- slot t-1
+        if constexpr (PAT == PAT_SEQ) {
+            const uint32_t upB = __shfl_sync(0xffffffffu, ovB[w], gbase + (t > 0 ? t - 1 : 0));
+            const uint32_t wrap = __shfl_sync(0xffffffffu, ovA[w], gbase + G - 1);
+            inB[w] = t > 0 ? upB : wrap;                            // slot G+t <- G+t-1
+        } else {
+            const uint32_t dn = __shfl_sync(0xffffffffu, ovB[w], gbase + (t < G - 1 ? t + 1 : G - 1));
+            inB[w] = t < G - 1 ? dn : ovA[w];                       // slot 2G-1-t <- 2G-2-t
+        }
+    }
+}
+
+// Turn completed slots (low B words already at OUT[s*B..], spill words at
+// P[s*(B+2)..]) into words OUT[s*B..s*B+B). in0: B+2 words added below slot 0 (a
+// carry coming from outside). xf may rewrite a slot sum first (add an addend,
+// double it ...). Returns the low word of everything above the last slot (its own
+// spill and overflow plus the resolved carry).
 template <class S, int B, int PAT, class XF>
 MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF &xf, uint32_t *OUT) {
+    static_assert(PAT == PAT_SEQ || PAT == PAT_ZIGZAG, "two slots per thread");
     constexpr int G = S::G;
-    constexpr int A = 2 * B + 2;
-    constexpr int NS = (PAT == PAT_ONE) ? 1 : 2;
-    constexpr int NSLOT = (PAT == PAT_ONE) ? G : 2 * G;
+    constexpr int SP = B + 2;
+    constexpr int NSLOT = 2 * G;
     uint32_t *Pm = g.P();
-    uint32_t *OV = g.OV();
-    uint32_t lo[NS][B];
-    uint32_t top = 0u;   // words at and above the last slot: its own spill + overflow (owner only)
+    uint32_t lo[2][B];
+    uint32_t top = 0u;   // words at and above the last slot (owner lane only)
 
     // 1. optional per-slot rewrite; keep the low B words
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
+    for (int k = 0; k < 2; ++k) {
         const int s = slot_of<G, PAT>(g.t, k);
-        uint32_t V[A];
-        lds<A>(V, Pm + s * A);
-        xf(s, V);
-        sts<A>(Pm + s * A, V);
+        uint32_t V[2 * B + 2];
+        {
+            uint32_t l[B], h[SP];
+            lds<B>(l, OUT + s * B);
+            lds<SP>(h, Pm + s * SP);
+#pragma unroll
+            for (int j = 0; j < B; ++j) V[j] = l[j];
+#pragma unroll
+            for (int j = 0; j < SP; ++j) V[B + j] = h[j];
+        }
+        if constexpr (XF::active) {
+            xf(s, V);
+            uint32_t h[SP];
+#pragma unroll
+            for (int j = 0; j < SP; ++j) h[j] = V[B + j];
+            sts<SP>(Pm + s * SP, h);
+        }
 #pragma unroll
         for (int j = 0; j < B; ++j) lo[k][j] = V[j];
         if (s == NSLOT - 1) top = V[B];
     }
-    gsync();
-    // 2. add the predecessor's spill (its words B..2B+1); overflow goes to OV
+    if constexpr (XF::active) gsync();
+    // 2. add the predecessor's spill
+    uint32_t ov[2][2];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
+    for (int k = 0; k < 2; ++k) {
         const int s = slot_of<G, PAT>(g.t, k);
-        uint32_t x[B + 2];
+        uint32_t x[SP];
         if (s == 0) {
 #pragma unroll
-            for (int j = 0; j < B + 2; ++j) x[j] = in0[j];
+            for (int j = 0; j < SP; ++j) x[j] = in0[j];
         } else {
-            const uint32_t *sp = Pm + (s - 1) * A + B;
-#pragma unroll
-            for (int j = 0; j < B + 2; ++j) x[j] = sp[j];
+            lds<SP>(x, Pm + (s - 1) * SP);
         }
         add_cc(x[0], lo[k][0]);
 #pragma unroll
@@ -197,20 +239,18 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
         addc(x[B + 1], 0u);
 #pragma unroll
         for (int j = 0; j < B; ++j) lo[k][j] = x[j];
-        OV[2 * s] = x[B];
-        OV[2 * s + 1] = x[B + 1];
+        ov[k][0] = x[B];
+        ov[k][1] = x[B + 1];
         if (s == NSLOT - 1) top += x[B];
     }
-    gsync();
     // 3. add the predecessor's overflow: leaves a 0/1 carry per slot
-    uint32_t cgen[NS], cprop[NS];
+    uint32_t oin[2][2];
+    pred_overflow<G, PAT>(g.t, g.gbase, ov[0], ov[1], oin[0], oin[1]);
+    uint32_t cgen[2], cprop[2];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        const int s = slot_of<G, PAT>(g.t, k);
-        uint32_t o0 = 0u, o1 = 0u;
-        if (s > 0) { o0 = OV[2 * s - 2]; o1 = OV[2 * s - 1]; }
-        add_cc(lo[k][0], o0);
-        addc_cc(lo[k][1], o1);
+    for (int k = 0; k < 2; ++k) {
+        add_cc(lo[k][0], oin[k][0]);
+        addc_cc(lo[k][1], oin[k][1]);
 #pragma unroll
         for (int j = 2; j < B; ++j) addc_cc(lo[k][j], 0u);
         cgen[k] = addc_get();
@@ -221,13 +261,13 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
     }
     // 4. carry-lookahead over the slots: carry into slot s = bit s of ((P + 2G) ^ P)
     const uint32_t gA = g.gbits(cgen[0] != 0u), pA = g.gbits(cprop[0] != 0u);
-    uint32_t gB = 0u, pB = 0u;
-    if constexpr (NS == 2) { gB = g.gbits(cgen[NS - 1] != 0u); pB = g.gbits(cprop[NS - 1] != 0u); }
+    const uint32_t gB = g.gbits(cgen[1] != 0u), pB = g.gbits(cprop[1] != 0u);
     const uint64_t Gm = slot_mask<G, PAT>(gA, gB);
     const uint64_t Pmask = slot_mask<G, PAT>(pA, pB);
     const uint64_t cin = (Pmask + (Gm << 1)) ^ Pmask;
+    gsync();   // every lane has read the spills it needs before OUT and P change again
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
+    for (int k = 0; k < 2; ++k) {
         const int s = slot_of<G, PAT>(g.t, k);
         add_word<B>(lo[k], (uint32_t)(cin >> s) & 1u);
         sts<B>(OUT + s * B, lo[k]);
@@ -251,12 +291,9 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
     for (int j = 0; j < G; ++j) {
         const int v = (g.t - j) & (G - 1);
         mac_block<M>(V, X + j * M, Y + v * M);
-        if (j == g.t) {
-            sts<A>(g.P() + g.t * A, V);
-            zero<A>(V);
-        }
+        if (j == g.t) flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
     }
-    sts<A>(g.P() + (G + g.t) * A, V);
+    flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
     gsync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
@@ -266,6 +303,7 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
 // slot sums of squaring: V = 2 * (cross products) + (squares of the blocks)
 template <class S>
 struct SqrXform {
+    static constexpr bool active = true;
     const uint32_t *D;
     template <int A>
     MPG_DI void operator()(int s, uint32_t (&V)[A]) const {
@@ -284,18 +322,13 @@ struct SqrXform {
     }
 };
 
-// T = X^2 (Alg. 2 structure): squares of the G blocks (one per thread, written
-// side by side to D, 2*NP words) plus twice the cross products X_u X_v, u < v.
-// Thread t owns slots t and G+t; slot s gets the pairs u < v with u + v = s.
+// T = X^2 (Alg. 2 structure): twice the cross products X_u X_v, u < v, plus the
+// squares of the G blocks. Thread t owns slots t and G+t (pairs u < v with
+// u + v = t and G + t). The block squares (one per thread) are formed after the
+// cross products and parked side by side in X and Y (2*NP words, free by then).
 template <class S>
-MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t *T) {
+MPG_DI void phase_sqr(const Grp<S> &g, uint32_t *X, uint32_t *T) {
     constexpr int G = S::G, M = S::M, A = S::A1;
-    {
-        uint32_t x[M], P[2 * M];
-        lds<M>(x, X + g.t * M);
-        block_mul<M>(P, x, x);
-        sts<2 * M>(D + 2 * g.t * M, P);
-    }
     const int nA = (g.t + 1) >> 1;              // pairs u < v with u + v = t
     const int nB = ((G - g.t + 1) >> 1) - 1;    // pairs with u + v = G + t
     constexpr int K = G / 2;                    // max of nA + nB over the group
@@ -304,8 +337,7 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     bool a_done = false;
     for (int j = 0; j < K; ++j) {
         if (j == nA) {
-            sts<A>(g.P() + g.t * A, V);
-            zero<A>(V);
+            flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
             a_done = true;
         }
         int u, v;
@@ -314,15 +346,17 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
         const bool live = j < nA + nB;
         mac_block<M>(V, X + (live ? u : 0) * M, live ? X + v * M : g.Z());
     }
-    if (!a_done) {
-        sts<A>(g.P() + g.t * A, V);
-        zero<A>(V);
-    }
-    sts<A>(g.P() + (G + g.t) * A, V);
+    if (!a_done) flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+    flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
+    uint32_t x[M], P[2 * M];
+    lds<M>(x, X + g.t * M);
+    gsync();                                    // all reads of X are done
+    block_mul<M>(P, x, x);
+    sts<2 * M>(X + 2 * g.t * M, P);
     gsync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
-    resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{D}, T);
+    resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{X}, T);
 }
 
 // Q = (X * Y) mod W^NP with half blocks (H words, 2G of them). Thread t owns
@@ -337,12 +371,9 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
         if (j <= g.t) { u = j; v = g.t - j; }
         else { u = j - g.t - 1; v = 2 * G - j; }
         mac_block<H>(V, X + u * H, Y + v * H);
-        if (j == g.t) {
-            sts<A>(g.P() + g.t * A, V);
-            zero<A>(V);
-        }
+        if (j == g.t) flush<H>(V, Q + g.t * H, g.P() + g.t * (H + 2));
     }
-    sts<A>(g.P() + (2 * G - 1 - g.t) * A, V);
+    flush<H>(V, Q + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
     gsync();
     uint32_t in0[H + 2];
     zero<H + 2>(in0);
@@ -351,6 +382,7 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
 
 template <int B>
 struct AddendXform {
+    static constexpr bool active = true;
     const uint32_t *Add;   // B words per slot
     template <int A>
     MPG_DI void operator()(int s, uint32_t (&V)[A]) const {
@@ -436,12 +468,9 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
         if (j < nA) { u = g.t + 1 + j; v = 2 * G + g.t - u; }
         else { u = j + 1; v = 4 * G - 2 - g.t - j; }
         mac_block<H>(V, Qs + u * H, Ns + v * H);
-        if (j == nA - 1) {
-            sts<A>(g.P() + g.t * A, V);
-            zero<A>(V);
-        }
+        if (j == nA - 1) flush<H>(V, C + g.t * H, g.P() + g.t * (H + 2));
     }
-    sts<A>(g.P() + (2 * G - 1 - g.t) * A, V);
+    flush<H>(V, C + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
     // sum Z over the group (butterfly; every lane gets the total)
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
@@ -468,19 +497,21 @@ MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *N
     constexpr int G = S::G, M = S::M, A = S::A1;
     uint32_t V[A];
     zero<A>(V);
+    const AddendXform<M> addT{T};
     for (int j = 0; j < G; ++j) {
         const int v = (g.t - j) & (G - 1);
         mac_block<M>(V, Qs + j * M, Ns + v * M);
-        if (j == g.t) {
-            sts<A>(g.P() + g.t * A, V);
-            zero<A>(V);
+        if (j == g.t) {   // add T's words of this slot, then store over them
+            addT(g.t, V);
+            flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
         }
     }
-    sts<A>(g.P() + (G + g.t) * A, V);
+    addT(G + g.t, V);
+    flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
     gsync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
-    return resolve<S, M, PAT_SEQ>(g, in0, AddendXform<M>{T}, T);
+    return resolve<S, M, PAT_SEQ>(g, in0, NoXform{}, T);
 }
 
 // OUT = (carry*R + C >= N) ? C - N : C, constant time. Borrows are resolved across
@@ -509,14 +540,20 @@ MPG_DI void cond_sub(const Grp<S> &g, const uint32_t *C, uint32_t carry, const u
     gsync();
 }
 
-// X <- X * Y * R^-1 mod N (or X^2 * R^-1 when square): X, Y, N, N' in shared memory.
-// red: 0 truncated (Alg. 6), 1 classical (Alg. 5).
+// Out-of-line steps of a Montgomery product. The exponentiation calls a product
+// from several places; one shared copy of each step keeps the instruction
+// footprint inside the instruction caches.
 template <class S>
-MPG_DI void mont_mul(const Grp<S> &g, bool square, int red) {
+__device__ __noinline__ void step_mul(Grp<S> g) { phase_mul<S>(g, g.X(), g.Y(), g.T()); }
+
+template <class S>
+__device__ __noinline__ void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.T()); }
+
+// T (2*NP words) -> X = T * R^-1 mod N (q goes to Y). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5).
+template <class S, int RED>
+__device__ __noinline__ void step_reduce(Grp<S> g) {
     constexpr int M = S::M, NP = S::NP;
     uint32_t *T = g.T();
-    if (square) phase_sqr<S>(g, g.X(), g.Y(), T);   // Y and Q hold the block squares
-    else phase_mul<S>(g, g.X(), g.Y(), T);
     // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0]
     uint32_t nz_all = 0u, nz_low = 0u;
     {
@@ -531,13 +568,24 @@ MPG_DI void mont_mul(const Grp<S> &g, bool square, int red) {
     const uint32_t c_add = g.gbits(nz_all != 0u) ? 1u : 0u;
     const uint32_t low_zero = g.gbits(nz_low != 0u) ? 0u : 1u;
     phase_mullo<S>(g, T, g.NI(), g.Q());
-    if (red == 0) {
+    if constexpr (RED == 0) {
         const uint32_t carry = phase_mulhi<S>(g, g.Q(), g.N(), T, c_add, low_zero, g.X());
         cond_sub<S>(g, g.X(), carry, g.N(), g.X());
     } else {
+        (void)c_add;
+        (void)low_zero;
         const uint32_t carry = phase_fma<S>(g, g.Q(), g.N(), T);
         cond_sub<S>(g, T + NP, carry, g.N(), g.X());
     }
+}
+
+// X <- X * Y * R^-1 mod N (or X^2 * R^-1 when square): X, Y, N, N' in shared memory.
+// Y is overwritten (it holds q afterwards).
+template <class S, int RED>
+MPG_DI void mont_mul(const Grp<S> &g, bool square) {
+    if (square) step_sqr<S>(g);
+    else step_mul<S>(g);
+    step_reduce<S, RED>(g);
 }
 
 }  // namespace mpg

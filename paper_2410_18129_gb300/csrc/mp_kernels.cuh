@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(TPB) k_mul(KArgs A) {
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
     gsync();
-    if (A.square) phase_sqr<S>(g, g.X(), g.Y(), g.T());
+    if (A.square) phase_sqr<S>(g, g.X(), g.T());
     else phase_mul<S>(g, g.X(), g.Y(), g.T());
     // store 2n words
     uint32_t x[2 * S::M];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(TPB) k_mul(KArgs A) {
 
 // ------------------------------------------------------------------ mont_mul / mont_sqr
 
-template <class S, int TPB>
+template <class S, int TPB, int RED>
 __global__ void __launch_bounds__(TPB) k_mont(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(TPB) k_mont(KArgs A) {
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
     gsync();
-    mont_mul<S>(g, A.square != 0, A.red);
+    mont_mul<S, RED>(g, A.square != 0);
     if (A.correct) {   // internal radix W^NP differs from the API radix W^n: multiply by W^(2NP-n) mod N
         load_ctx<S>(g, g.Y(), A.K, A, k, valid);
         gsync();
-        mont_mul<S>(g, false, A.red);
+        mont_mul<S, RED>(g, false);
     }
     uint32_t x[S::M];
     lds<S::M>(x, g.X() + g.t * S::M);
@@ -185,7 +185,7 @@ MPG_DI uint32_t window_bits(const KArgs &A, size_t k, bool valid, int pos, int w
     return v;
 }
 
-template <class S, int TPB>
+template <class S, int TPB, int RED>
 __global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
     constexpr int M = S::M, NP = S::NP;
     extern __shared__ uint4 smem4[];
@@ -216,34 +216,46 @@ __global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
         }
     };
 
+    auto get = [&](int e, uint32_t *dst) {   // this thread's M words of table entry e
+        uint32_t x[M];
+        if constexpr (M % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < M / 4; ++c) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, k, batch)];
+                x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const int i = g.t * M + j;
+                x[j] = valid ? A.table[tidx4<S>(e, i >> 2, k, batch) * 4 + (i & 3)] : 0u;
+            }
+        }
+        sts<M>(dst + g.t * M, x);
+    };
+
     init_zero_block<S>(g);
     load_ctx<S>(g, g.N(), A.N, A, k, valid);
     load_ctx<S>(g, g.NI(), A.NI, A, k, valid);
     load_api<S>(g, g.X(), A.a, A, k, valid);
     load_ctx<S>(g, g.Y(), A.R2, A, k, valid);
     gsync();
-    mont_mul<S>(g, false, A.red);                 // X = a*R mod N = G[1]
+    mont_mul<S, RED>(g, false);                 // X = a*R mod N = G[1]
     put(1, g.X());
-    {   // Y = G[1]; G[0] = R mod N
-        uint32_t x[M];
-        lds<M>(x, g.X() + g.t * M);
-        sts<M>(g.Y() + g.t * M, x);
-        load_ctx<S>(g, g.X(), A.R1, A, k, valid);
-        gsync();
-        put(0, g.X());
-        lds<M>(x, g.Y() + g.t * M);
-        sts<M>(g.X() + g.t * M, x);
-        gsync();
-    }
+    load_ctx<S>(g, g.Y(), A.R1, A, k, valid);     // G[0] = R mod N
+    put(0, g.Y());
     for (int e = 2; e < E; ++e) {                 // G[e] = G[e-1] * G[1]
-        mont_mul<S>(g, false, A.red);
+        get(1, g.Y());                            // (the product leaves q in Y)
+        gsync();
+        mont_mul<S, RED>(g, false);
         put(e, g.X());
     }
     load_ctx<S>(g, g.X(), A.R1, A, k, valid);     // Y_acc = 1 in Montgomery form
     gsync();
     const int windows = (A.ebits + w - 1) / w;
     for (int win = windows - 1; win >= 0; --win) {
-        for (int s = 0; s < w; ++s) mont_mul<S>(g, true, A.red);
+        for (int s = 0; s < w; ++s) mont_mul<S, RED>(g, true);
         const uint32_t bsel = window_bits(A, k, valid, win * w, w);
         // masked scan of the whole table: every entry is read, one is kept
         uint32_t acc[M];
@@ -270,7 +282,7 @@ __global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
         }
         sts<M>(g.Y() + g.t * M, acc);
         gsync();
-        mont_mul<S>(g, false, A.red);
+        mont_mul<S, RED>(g, false);
     }
     {   // leave the Montgomery domain: X * 1 * R^-1
         uint32_t x[M];
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
         if (g.t == 0) x[0] = 1u;
         sts<M>(g.Y() + g.t * M, x);
         gsync();
-        mont_mul<S>(g, false, A.red);
+        mont_mul<S, RED>(g, false);
     }
     uint32_t x[M];
     lds<M>(x, g.X() + g.t * M);
@@ -315,8 +327,12 @@ static cudaError_t launch_k(F kern, const KArgs &A, cudaStream_t st) {
 template <class S, int TPB>
 struct ShapeImpl {
     static cudaError_t mul(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 0>(k_mul<S, TPB>, A, st); }
-    static cudaError_t mont(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 1>(k_mont<S, TPB>, A, st); }
-    static cudaError_t modexp(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 2>(k_modexp<S, TPB>, A, st); }
+    static cudaError_t mont(const KArgs &A, cudaStream_t st) {
+        return A.red ? launch_k<S, TPB, 3>(k_mont<S, TPB, 1>, A, st) : launch_k<S, TPB, 1>(k_mont<S, TPB, 0>, A, st);
+    }
+    static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
+        return A.red ? launch_k<S, TPB, 4>(k_modexp<S, TPB, 1>, A, st) : launch_k<S, TPB, 2>(k_modexp<S, TPB, 0>, A, st);
+    }
     static ShapeOps ops() {
         return ShapeOps{S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont, &modexp};
     }
