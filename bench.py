@@ -132,7 +132,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--quick", action="store_true",
                     help="time the modexp steps only (no comparison runs, no e2e, no CPU baseline): for profiling")
+    ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096"],
+                    help="batch_2048: the headline line; batch_4096: 4096-bit products (schoolbook vs "
+                         "Karatsuba, 4108/4154 edges), Montgomery and w=6 modexp")
     args = ap.parse_args()
+    if args.workload == "batch_4096":
+        return bench_4096(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,6 +333,91 @@ def main():
     ctx.free()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _event_timer(torch, stream):
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+    return timed
+
+
+def bench_4096(args):
+    """4096-bit workload (16384 instances): products schoolbook vs one-level Karatsuba, the
+    4108-bit (schoolbook) and 4154-bit (Karatsuba) edge sizes, truncated Montgomery products and
+    the w=6 constant-time modexp. One JSON line; `value` is 4096-bit modexp/s."""
+    import numpy as np
+    import seeded_inputs as si
+    import torch
+    import paper_2410_18129_gb300 as mp
+    import oracle
+
+    B = 16384 if args.batch == 65536 else args.batch
+    IL = mp.LAYOUT_INTERLEAVED
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    timed = _event_timer(torch, stream)
+    out = {}
+    prod = {}
+    for bits in (4096, 4108, 4154):
+        b = si.batch_4096(0, B, bits)
+        n = b.n
+        A, Bv = mp.to_device(mp.interleave(b.a)), mp.to_device(mp.interleave(b.b))
+        C = torch.zeros(mp.array_words(IL, B, 2 * n), dtype=torch.int32, device="cuda")
+        for algo, nm in ((mp.ALGO_SCHOOLBOOK, "schoolbook"), (mp.ALGO_KARATSUBA, "karatsuba")):
+            for op in ("mul", "sqr"):
+                f = (lambda: mp.mp_mul(C, A, Bv, B, bits, IL, algo)) if op == "mul" else \
+                    (lambda: mp.mp_sqr(C, A, B, bits, IL, algo))
+                for _ in range(args.warmup):
+                    f()
+                ms = timed(f, max(3, args.steps))
+                prod[f"{op}_{nm}_{bits}"] = B / (ms / 1e3)
+                # bit-exact spot check against the oracle
+                got = mp.deinterleave(mp.to_host(C), B, 2 * n)[:16]
+                want = oracle.mul(b.a[:16], b.b[:16]) if op == "mul" else oracle.sqr(b.a[:16])
+                assert np.array_equal(got, want), (op, nm, bits)
+    out["products_per_s"] = prod
+    b = si.batch_4096(0, B, 4096)
+    n = b.n
+    N, A, Bv, E = (mp.to_device(mp.interleave(x)) for x in (b.N, b.a, b.b, b.e))
+    ctx = mp.MontCtx(N, B, 4096, IL)
+    C = torch.zeros_like(A)
+    mm = {}
+    for red, nm in ((mp.RED_TRUNCATED, "trunc"), (mp.RED_FULL, "full")):
+        for _ in range(3):
+            mp.mont_mul(C, A, Bv, ctx, red)
+        mm["mul_" + nm] = B / (timed(lambda: mp.mont_mul(C, A, Bv, ctx, red), 20) / 1e3)
+        mm["sqr_" + nm] = B / (timed(lambda: mp.mont_sqr(C, A, ctx, red), 20) / 1e3)
+    out["mont_per_s"] = mm
+    ws = torch.empty(mp.modexp_workspace_bytes(B, 4096, 6) // 4, dtype=torch.int32, device="cuda")
+    Y = torch.zeros_like(A)
+    step = lambda: mp.modexp_consttime(Y, A, E, b.ebits, ctx, 6, mp.RED_TRUNCATED, workspace=ws)
+    for _ in range(args.warmup):
+        step()
+    with ClockSampler(0) as clk:
+        ms = timed(step, args.steps)
+    idx = np.linspace(0, B - 1, 6).astype(int)
+    got = mp.deinterleave(mp.to_host(Y), B, n)[idx]
+    want = oracle.modexp(b.a[idx], b.e[idx], b.ebits, b.N[idx])
+    line = {
+        "metric": "4096-bit const-time modexp/s (w=6) and 4096-bit product rates", "value": B / (ms / 1e3),
+        "unit": "modexp/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"batch_4096: {B} x 4096-bit random odd moduli, full-length exponents, w=6; "
+                               "products at 4096/4108/4154 bits", "batch": B},
+        "clocks": clk.summary(), "parity": {"sampled": int(idx.size),
+                                            "mismatches": int((got != want).any(axis=1).sum())},
+        **out,
+    }
+    print(json.dumps(line))
+    ctx.free()
 
 
 if __name__ == "__main__":

@@ -75,8 +75,9 @@ int mp_convert(uint32_t *dst, mp_layout dst_layout, const uint32_t *src, mp_layo
 /*
  * Batch product C_k = A_k * B_k (Alg. 1 B_mul; Sec. 3 one-level Karatsuba).
  * a, b: n words per instance; c: 2n words per instance; all in `layout`.
- * algo: SCHOOLBOOK, KARATSUBA (one level; needs bits >= 1024) or AUTO
- * (Karatsuba from 4096 bits up). c must not overlap a or b.
+ * algo: SCHOOLBOOK, KARATSUBA (one level, Sec. 3: three half-size products; sizes
+ * above 512 bits, else MP_ERR_UNIMPLEMENTED) or AUTO (Karatsuba above 4096 bits).
+ * c must not overlap a or b.
  */
 int mp_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,
            mp_layout layout, mp_algo algo, void *stream);

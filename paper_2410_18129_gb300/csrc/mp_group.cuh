@@ -34,7 +34,8 @@ struct Shape {
     static constexpr int A1 = 2 * M + 2;   // slot accumulator words, full blocks
     static constexpr int A2 = 2 * H + 2;   // slot accumulator words, half blocks
     static_assert(G >= 2 && G <= 16 && (G & (G - 1)) == 0, "G must be 2, 4, 8 or 16");
-    static_assert(M >= 4 && M % 2 == 0, "M must be even and >= 4");
+    static_assert(M >= 2, "M must be >= 2");
+    static constexpr bool MONT_OK = (M >= 4 && M % 2 == 0);   // half blocks of >= 2 words
     // per-instance shared memory map (32-bit words)
     static constexpr int OFF_X = 0;               // operand / result; X and Y together hold the block squares
     static constexpr int OFF_Y = NP;              // operand, then q
@@ -51,6 +52,8 @@ struct Shape {
 template <class S>
 struct Grp {
     uint32_t *sm;   // this instance's shared words
+    uint32_t *pa;   // slot spill area (2G slots of M+2 words)
+    uint32_t *za;   // M zero words
     int t;          // thread index in the group
     int gbase;      // warp lane of thread 0 of the group
     MPG_DI uint32_t *X() const { return sm + S::OFF_X; }
@@ -59,8 +62,8 @@ struct Grp {
     MPG_DI uint32_t *N() const { return sm + S::OFF_N; }
     MPG_DI uint32_t *NI() const { return sm + S::OFF_NI; }
     MPG_DI uint32_t *T() const { return sm + S::OFF_T; }
-    MPG_DI uint32_t *P() const { return sm + S::OFF_P; }
-    MPG_DI uint32_t *Z() const { return sm + S::OFF_Z; }
+    MPG_DI uint32_t *P() const { return pa; }
+    MPG_DI uint32_t *Z() const { return za; }
     // this group's bits of a warp ballot
     MPG_DI uint32_t gbits(bool pred) const {
         return (__ballot_sync(0xffffffffu, pred) >> gbase) & ((1u << S::G) - 1u);
@@ -325,9 +328,9 @@ struct SqrXform {
 // T = X^2 (Alg. 2 structure): twice the cross products X_u X_v, u < v, plus the
 // squares of the G blocks. Thread t owns slots t and G+t (pairs u < v with
 // u + v = t and G + t). The block squares (one per thread) are formed after the
-// cross products and parked side by side in X and Y (2*NP words, free by then).
+// cross products and parked side by side in D (2*NP words; D may overlap X).
 template <class S>
-MPG_DI void phase_sqr(const Grp<S> &g, uint32_t *X, uint32_t *T) {
+MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t *T) {
     constexpr int G = S::G, M = S::M, A = S::A1;
     const int nA = (g.t + 1) >> 1;              // pairs u < v with u + v = t
     const int nB = ((G - g.t + 1) >> 1) - 1;    // pairs with u + v = G + t
@@ -352,17 +355,18 @@ MPG_DI void phase_sqr(const Grp<S> &g, uint32_t *X, uint32_t *T) {
     lds<M>(x, X + g.t * M);
     gsync();                                    // all reads of X are done
     block_mul<M>(P, x, x);
-    sts<2 * M>(X + 2 * g.t * M, P);
+    sts<2 * M>(D + 2 * g.t * M, P);
     gsync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
-    resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{X}, T);
+    resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{D}, T);
 }
 
 // Q = (X * Y) mod W^NP with half blocks (H words, 2G of them). Thread t owns
 // slots t and 2G-1-t: t+1 and 2G-t block products, 2G+1 for every thread.
 template <class S>
 MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
+    static_assert(S::MONT_OK, "Montgomery needs an even M >= 4");
     constexpr int G = S::G, H = S::H, A = S::A2;
     uint32_t V[A];
     zero<A>(V);
@@ -547,7 +551,7 @@ template <class S>
 __device__ __noinline__ void step_mul(Grp<S> g) { phase_mul<S>(g, g.X(), g.Y(), g.T()); }
 
 template <class S>
-__device__ __noinline__ void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.T()); }
+__device__ __noinline__ void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // squares in X, Y
 
 // T (2*NP words) -> X = T * R^-1 mod N (q goes to Y). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5).
 template <class S, int RED>

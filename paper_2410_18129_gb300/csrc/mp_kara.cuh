@@ -1,0 +1,151 @@
+// One level of Karatsuba for batched products and squares (Sec. 3):
+//   A = a_l + W^h a_h, B = b_l + W^h b_h,  h = NP/2 words
+//   D0 = a_l b_l,  D2 = a_h b_h,  D1 = (a_l + a_h)(b_l + b_h)
+//   A*B = D0 + W^h (D1 - D0 - D2) + W^2h D2
+// The three half-size products run one after the other on the whole group with
+// the schoolbook block products of a half shape HS (same G, M/2 words per
+// thread). a_l + a_h has h words plus a carry bit c_a; with s_a, s_b the low h
+// words, D1 = s_a s_b + W^h (c_a s_b + c_b s_a) + W^2h c_a c_b. Every sum and
+// difference runs across the group with the same carry-lookahead as elsewhere.
+#pragma once
+#include "mp_kernels.cuh"
+
+namespace mpg {
+
+// dst[i] = a[i] + b(i) for i < G*C (thread t owns words [t*C, t*C+C)), plus carry-in
+// cin (0/1, group-uniform). Returns the carry out of the top word (group-uniform).
+// b is a functor word index -> word. dst may equal a.
+template <class S, int C, class BF>
+MPG_DI uint32_t gadd(const Grp<S> &g, uint32_t *dst, const uint32_t *a, const BF &b, uint32_t cin) {
+    constexpr int G = S::G;
+    uint32_t x[C];
+    lds<C>(x, a + g.t * C);
+    add_cc(x[0], b(g.t * C));
+#pragma unroll
+    for (int j = 1; j < C; ++j) addc_cc(x[j], b(g.t * C + j));
+    const uint32_t gen = addc_get();
+    uint32_t all = x[0];
+#pragma unroll
+    for (int j = 1; j < C; ++j) all &= x[j];
+    const uint64_t Gm = g.gbits(gen != 0u), Pm = g.gbits(all == 0xffffffffu);
+    const uint64_t in = (Pm + ((Gm << 1) | (uint64_t)cin)) ^ Pm;
+    add_word<C>(x, (uint32_t)(in >> g.t) & 1u);
+    gsync();
+    sts<C>(dst + g.t * C, x);
+    gsync();
+    return (uint32_t)(in >> G) & 1u;
+}
+
+// dst[i] = a[i] - b[i] for i < G*C; returns the borrow out of the top word.
+template <class S, int C>
+MPG_DI uint32_t gsub(const Grp<S> &g, uint32_t *dst, const uint32_t *a, const uint32_t *b) {
+    constexpr int G = S::G;
+    uint32_t x[C], y[C];
+    lds<C>(x, a + g.t * C);
+    lds<C>(y, b + g.t * C);
+    uint32_t eq = 0u;
+#pragma unroll
+    for (int j = 0; j < C; ++j) eq |= x[j] ^ y[j];
+    const uint32_t gen = sub_n<C>(x, y);
+    const uint64_t Gm = g.gbits(gen != 0u), Pm = g.gbits(eq == 0u);
+    const uint64_t bin = (Pm + (Gm << 1)) ^ Pm;
+    sub_word<C>(x, (uint32_t)(bin >> g.t) & 1u);
+    gsync();
+    sts<C>(dst + g.t * C, x);
+    gsync();
+    return (uint32_t)(bin >> G) & 1u;
+}
+
+// shared-memory map of one instance (words), h = HS::NP
+template <class F, class HS>
+struct KaraLayout {
+    static constexpr int h = HS::NP;
+    static_assert(2 * h == F::NP && HS::G == F::G, "HS must be F with half the words per thread");
+    static constexpr int OFF_A = 0;            // a (2h)
+    static constexpr int OFF_B = 2 * h;        // b (2h)
+    static constexpr int OFF_SA = 4 * h;       // a_l + a_h (h)
+    static constexpr int OFF_SB = 5 * h;       // b_l + b_h (h)
+    static constexpr int OFF_D = 6 * h;        // D0 | D2 (4h): the result is formed in place
+    static constexpr int OFF_D1 = 10 * h;      // D1, then D1 - D0 - D2 (2h)
+    static constexpr int OFF_SQ = 12 * h;      // block squares of a half product (2h)
+    static constexpr int OFF_P = 14 * h;       // slot spills of the half products
+    static constexpr int OFF_Z = OFF_P + 2 * HS::G * (HS::M + 2);
+    static constexpr int WORDS = (OFF_Z + HS::M + 3) & ~3;
+};
+
+template <class F, class HS, int TPB>
+__global__ void __launch_bounds__(TPB) k_kara(KArgs A) {
+    using L = KaraLayout<F, HS>;
+    constexpr int h = L::h, MH = HS::M;
+    extern __shared__ uint4 smem4[];
+    uint32_t *sm = reinterpret_cast<uint32_t *>(smem4) + (threadIdx.x / F::G) * L::WORDS;
+    Grp<HS> g;
+    g.sm = sm;
+    g.pa = sm + L::OFF_P;
+    g.za = sm + L::OFF_Z;
+    g.t = threadIdx.x % F::G;
+    g.gbase = (threadIdx.x & 31) & ~(F::G - 1);
+    const size_t k = (size_t)blockIdx.x * (TPB / F::G) + threadIdx.x / F::G;
+    const bool valid = k < A.batch;
+    uint32_t *a = sm + L::OFF_A, *b = sm + L::OFF_B, *sa = sm + L::OFF_SA, *sb = sm + L::OFF_SB;
+    uint32_t *D = sm + L::OFF_D, *D1 = sm + L::OFF_D1, *SQ = sm + L::OFF_SQ;
+    if (g.t == 0) {
+#pragma unroll
+        for (int j = 0; j < MH; ++j) g.za[j] = 0u;
+    }
+    {
+        uint32_t x[F::M];
+        gload<F::M>(x, A.a, A.layout, k, valid, g.t * F::M, A.n, A.batch);
+        sts<F::M>(a + g.t * F::M, x);
+        if (!A.square) {
+            gload<F::M>(x, A.b, A.layout, k, valid, g.t * F::M, A.n, A.batch);
+            sts<F::M>(b + g.t * F::M, x);
+        }
+    }
+    gsync();
+    const uint32_t ca = gadd<HS, MH>(g, sa, a, [&](int i) { return a[h + i]; }, 0u);
+    uint32_t cb = ca;
+    if (!A.square) cb = gadd<HS, MH>(g, sb, b, [&](int i) { return b[h + i]; }, 0u);
+    const uint32_t *sbp = A.square ? sa : sb;
+    if (A.square) {
+        phase_sqr<HS>(g, a, SQ, D);               // D0 = a_l^2
+        phase_sqr<HS>(g, a + h, SQ, D + 2 * h);   // D2 = a_h^2
+        phase_sqr<HS>(g, sa, SQ, D1);             // D1 = s_a^2
+    } else {
+        phase_mul<HS>(g, a, b, D);                // D0 = a_l b_l
+        phase_mul<HS>(g, a + h, b + h, D + 2 * h);   // D2 = a_h b_h
+        phase_mul<HS>(g, sa, sb, D1);             // D1 = s_a s_b
+    }
+    // D1 <- D1 + W^h (c_a s_b + c_b s_a) + W^2h c_a c_b - D0 - D2   (2h words + top word)
+    const uint32_t ma = 0u - ca, mb = 0u - cb;
+    uint32_t top = gadd<HS, 2 * MH>(g, D1, D1, [&](int i) { return i >= h ? (sbp[i - h] & ma) : 0u; }, 0u);
+    top += gadd<HS, 2 * MH>(g, D1, D1, [&](int i) { return i >= h ? (sa[i - h] & mb) : 0u; }, 0u);
+    top += ca & cb;
+    top -= gsub<HS, 2 * MH>(g, D1, D1, D);
+    top -= gsub<HS, 2 * MH>(g, D1, D1, D + 2 * h);
+    // result = (D2 : D0) + W^h (D1 + W^2h top)
+    gadd<HS, 4 * MH>(g, D, D, [&](int i) {
+        return (i >= h && i < 3 * h) ? D1[i - h] : (i == 3 * h ? top : 0u);
+    }, 0u);
+    uint32_t x[2 * F::M];
+    lds<2 * F::M>(x, D + 2 * g.t * F::M);
+    gstore<2 * F::M>(A.out, x, A.layout, k, valid, 2 * g.t * F::M, 2 * A.n, A.batch);
+}
+
+template <class F, class HS, int TPB>
+static cudaError_t launch_kara(const KArgs &A, cudaStream_t st) {
+    using L = KaraLayout<F, HS>;
+    constexpr int GPB = TPB / F::G;
+    const size_t smem = (size_t)GPB * L::WORDS * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_kara<F, HS, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const size_t blocks = (A.batch + GPB - 1) / GPB;
+    k_kara<F, HS, TPB><<<(unsigned)blocks, TPB, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace mpg

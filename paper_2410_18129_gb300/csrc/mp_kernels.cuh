@@ -93,6 +93,8 @@ MPG_DI Grp<S> make_group(uint32_t *smem) {
     Grp<S> g;
     const int gi = threadIdx.x / S::G;
     g.sm = smem + gi * S::WORDS;
+    g.pa = g.sm + S::OFF_P;
+    g.za = g.sm + S::OFF_Z;
     g.t = threadIdx.x % S::G;
     g.gbase = (threadIdx.x & 31) & ~(S::G - 1);
     return g;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(TPB) k_mul(KArgs A) {
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
     gsync();
-    if (A.square) phase_sqr<S>(g, g.X(), g.T());
+    if (A.square) phase_sqr<S>(g, g.X(), g.X(), g.T());   // squares in X, Y
     else phase_mul<S>(g, g.X(), g.Y(), g.T());
     // store 2n words
     uint32_t x[2 * S::M];
@@ -306,6 +308,7 @@ struct ShapeOps {
     cudaError_t (*mul)(const KArgs &, cudaStream_t);
     cudaError_t (*mont)(const KArgs &, cudaStream_t);
     cudaError_t (*modexp)(const KArgs &, cudaStream_t);
+    cudaError_t (*kara)(const KArgs &, cudaStream_t);   // one-level Karatsuba product, or null
 };
 
 // KIND tells the kernels of one shape apart, so that each gets its own attribute call
@@ -334,7 +337,7 @@ struct ShapeImpl {
         return A.red ? launch_k<S, TPB, 4>(k_modexp<S, TPB, 1>, A, st) : launch_k<S, TPB, 2>(k_modexp<S, TPB, 0>, A, st);
     }
     static ShapeOps ops() {
-        return ShapeOps{S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont, &modexp};
+        return ShapeOps{S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont, &modexp, nullptr};
     }
 };
 
@@ -343,4 +346,14 @@ struct ShapeImpl {
 #define MPG_DEFINE_SHAPE(G, M, TPB)                                              \
     namespace mpg {                                                              \
     ShapeOps shape_ops_##G##_##M() { return ShapeImpl<Shape<G, M>, TPB>::ops(); } \
+    }
+
+// a shape whose products can also run as one level of Karatsuba over the half shape (G, MH)
+#define MPG_DEFINE_SHAPE_KARA(G, M, TPB, MH, TPBK)                                           \
+    namespace mpg {                                                                          \
+    ShapeOps shape_ops_##G##_##M() {                                                         \
+        ShapeOps o = ShapeImpl<Shape<G, M>, TPB>::ops();                                     \
+        o.kara = &launch_kara<Shape<G, M>, Shape<G, MH>, TPBK>;                              \
+        return o;                                                                            \
+    }                                                                                        \
     }

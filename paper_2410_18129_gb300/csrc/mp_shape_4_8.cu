@@ -1,3 +1,4 @@
 // Kernels for groups of 4 threads x 8 words per thread (32 words, 1024 bits), 256 threads per block.
-#include "mp_kernels.cuh"
-MPG_DEFINE_SHAPE(4, 8, 256)
+#include "mp_kara.cuh"
+MPG_DEFINE_SHAPE_KARA(4, 8, 256, 4, 256)
+// Karatsuba: three half products on groups of 4 threads x 4 words, 256 threads per block.

@@ -252,3 +252,43 @@ def test_convert_round_trip(mp, w):
     assert bad.size == 0, f"{bad.size} words differ, first at {bad[:6]}: got {got[bad[:6]]} want {want[bad[:6]]}"
     mp.mp_convert(back, IM, mid, IL, batch, w)
     assert (mp.to_host(back).reshape(batch, w) == x).all()
+
+
+# ------------------------------------------------------------------ one-level Karatsuba
+
+@pytest.mark.parametrize("bits", [520, 1000, 1024, 2048, 2078, 3072, 4096, 4108, 4154])
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_karatsuba_mul_sqr(mp, bits, layout):
+    batch = 45 if bits > 3000 else 173
+    a_np = si.random_bits(si.stream(0, "test", "other", 5000 + bits), batch, bits)
+    b_np = si.random_bits(si.stream(0, "test", "other", 6000 + bits), batch, bits)
+    n = a_np.shape[1]
+    a_np[0] = 0xFFFFFFFF                        # all-ones: the half sums carry out
+    b_np[0] = 0xFFFFFFFF
+    if bits % 32:
+        a_np[0, n - 1] = (1 << (bits % 32)) - 1
+        b_np[0, n - 1] = (1 << (bits % 32)) - 1
+    a_np[1] = 0
+    A, B = dev(mp, a_np, layout), dev(mp, b_np, layout)
+    C = out_tensor(mp, batch, 2 * n, layout)
+    mp.mp_mul(C, A, B, batch, bits, layout, mp.ALGO_KARATSUBA)
+    assert_equal(host(mp, C, batch, 2 * n, layout), oracle.mul(a_np, b_np), f"karatsuba mul {bits}")
+    mp.mp_sqr(C, A, batch, bits, layout, mp.ALGO_KARATSUBA)
+    assert_equal(host(mp, C, batch, 2 * n, layout), oracle.sqr(a_np), f"karatsuba sqr {bits}")
+
+
+def test_karatsuba_auto_and_small_sizes(mp):
+    bits, batch = 4096, 9
+    x = si.random_bits(si.stream(0, "test", "other", 77), batch, bits)
+    C = out_tensor(mp, batch, 2 * 128, IM)
+    mp.mp_mul(C, dev(mp, x, IM), dev(mp, x, IM), batch, bits, IM, mp.ALGO_AUTO)
+    assert_equal(host(mp, C, batch, 256, IM), oracle.sqr(x), "auto 4096")
+    y = si.random_bits(si.stream(0, "test", "other", 79), batch, 4154)
+    C2 = out_tensor(mp, batch, 2 * 130, IM)
+    mp.mp_sqr(C2, dev(mp, y, IM), batch, 4154, IM, mp.ALGO_AUTO)
+    assert_equal(host(mp, C2, batch, 260, IM), oracle.sqr(y), "auto 4154 (karatsuba)")
+    small = si.random_bits(si.stream(0, "test", "other", 78), 4, 256)
+    with pytest.raises(mp.MpError) as e:
+        mp.mp_mul(out_tensor(mp, 4, 16, IM), dev(mp, small, IM), dev(mp, small, IM), 4, 256, IM,
+                  mp.ALGO_KARATSUBA)
+    assert e.value.status == -7
