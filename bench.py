@@ -132,12 +132,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--quick", action="store_true",
                     help="time the modexp steps only (no comparison runs, no e2e, no CPU baseline): for profiling")
-    ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096"],
+    ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096", "mixed"],
                     help="batch_2048: the headline line; batch_4096: 4096-bit products (schoolbook vs "
                          "Karatsuba, 4108/4154 edges), Montgomery and w=6 modexp")
     args = ap.parse_args()
     if args.workload == "batch_4096":
         return bench_4096(args)
+    if args.workload == "mixed":
+        return bench_mixed(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -418,6 +420,108 @@ def bench_4096(args):
     }
     print(json.dumps(line))
     ctx.free()
+
+
+def bench_mixed(args):
+    """Mixed sizes: 100000 exponentiations, 40% 2048 / 25% 1024 / 20% 3072 / 15% 4096 bits,
+    full-length exponents. The autotuner picks shape and window per size; then three forms are
+    timed: one launch per size (plain), one persistent launch over all sizes, and that launch
+    replayed from a CUDA graph together with the host->device input copies and the result copy
+    (end to end). One JSON line; `value` is the persistent launch's modexp/s."""
+    import numpy as np
+    import seeded_inputs as si
+    import torch
+    import paper_2410_18129_gb300 as mp
+    from paper_2410_18129_gb300 import tune
+    import oracle
+
+    total = 100000 if args.batch == 65536 else args.batch
+    sizes = si.mixed_sizes(0, total)
+    classes = [(bits, int((sizes == bits).sum())) for bits in (4096, 3072, 2048, 1024)]
+    batches = {bits: si.make_batch(0, "mixed", cnt, bits, sub=bits) for bits, cnt in classes}
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    timed = _event_timer(torch, stream)
+    choice = tune.load_or_tune(sizes=(1024, 2048, 3072, 4096))
+    IL = mp.LAYOUT_INTERLEAVED
+    dev = lambda x: mp.to_device(mp.interleave(x))
+    jobs, ctxs, plain_ws, host = [], [], {}, []
+    for bits, cnt in classes:
+        b = batches[bits]
+        ctx = mp.MontCtx(dev(b.N), cnt, bits, IL)
+        A, E = dev(b.a), dev(b.e)
+        Y = torch.zeros_like(A)
+        jobs.append((Y, A, E, bits, ctx, 0))
+        ctxs.append(ctx)
+        w = choice[str(bits)]["window"]
+        plain_ws[bits] = torch.empty(mp.modexp_workspace_bytes(cnt, bits, w) // 4, dtype=torch.int32, device="cuda")
+        host.append((torch.from_numpy(mp.interleave(b.a).view(np.int32)).pin_memory(),
+                     torch.from_numpy(mp.interleave(b.e).view(np.int32)).pin_memory(),
+                     torch.empty(Y.numel(), dtype=torch.int32).pin_memory()))
+    ws = mp.mixed_workspace(jobs)
+
+    def plain():
+        for (Y, A, E, bits, ctx, w), (_, cnt) in zip(jobs, classes):
+            mp.modexp_consttime(Y, A, E, bits, ctx, 0, workspace=plain_ws[bits])
+
+    def mixed():
+        mp.modexp_consttime_mixed(jobs, mp.RED_TRUNCATED, ws)
+
+    def e2e():
+        for (Y, A, E, *_), (hA, hE, hY) in zip(jobs, host):
+            A.copy_(hA, non_blocking=True)
+            E.copy_(hE, non_blocking=True)
+        mixed()
+        for (Y, *_), (hA, hE, hY) in zip(jobs, host):
+            hY.copy_(Y, non_blocking=True)
+
+    for _ in range(args.warmup):
+        plain()
+        mixed()
+        e2e()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        e2e()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        e2e()
+    k = max(2, args.steps)
+    ms_plain = timed(plain, k)
+    with ClockSampler(0) as clk:
+        ms_mixed = timed(mixed, k)
+    ms_graph = timed(graph.replay, k)
+    # parity: each size class, sampled instances of the graph-replayed results vs the oracle
+    torch.cuda.synchronize()
+    mism, sampled = 0, 0
+    for (bits, cnt), (hA, hE, hY) in zip(classes, host):
+        b = batches[bits]
+        got = mp.deinterleave(hY.numpy().view(np.uint32), cnt, b.n)
+        idx = np.linspace(0, cnt - 1, 4).astype(int)
+        want = oracle.modexp(b.a[idx], b.e[idx], b.ebits, b.N[idx])
+        mism += int((got[idx] != want).any(axis=1).sum())
+        sampled += idx.size
+    h2d = sum((hA.numel() + hE.numel()) * 4 for hA, hE, _ in host)
+    d2h = sum(hY.numel() * 4 for *_, hY in host)
+    line = {
+        "metric": "mixed-size const-time modexp/s (one persistent launch; CUDA graph end to end)",
+        "value": total / (ms_mixed / 1e3), "unit": "modexp/s", "n_gpus": 1, "steps": k, "warmup": args.warmup,
+        "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"mixed: {total} modexp, sizes " + ", ".join(f"{c} x {b}" for b, c in classes)
+                               + " bits, random odd moduli, full-length exponents, truncated Montgomery",
+                   "tuned": {b: {k2: v for k2, v in c.items() if k2 != "timings"} for b, c in choice.items()}},
+        "plain_per_size_launches_per_s": total / (ms_plain / 1e3),
+        "e2e": {"value": total / (ms_graph / 1e3), "unit": "modexp/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "form": "CUDA graph: H2D copies + persistent launch + D2H copies"},
+        "gpu_launches": 1, "clocks": clk.summary(), "parity": {"sampled": sampled, "mismatches": mism},
+    }
+    print(json.dumps(line))
+    for c in ctxs:
+        c.free()
 
 
 if __name__ == "__main__":

@@ -148,6 +148,44 @@ int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uin
                      void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Mixed-size batches in one persistent launch (pattern (2) of the serving/batching
+ * use of Alg. 7): each job is one context's batch of exponentiations, with its own
+ * operand size, exponent length and window (0 = tuned), run with the group shape
+ * selected for its size. Jobs of up to 4096 bits (padded sizes 512/1024/2048/3072/
+ * 4096 bits), at most 16 per call. All jobs run in
+ * ONE kernel launch: blocks pull tiles of instances from an atomic counter, the
+ * costliest job first, so the launch can be captured in a CUDA graph together with
+ * its input copies. Results equal those of modexp_consttime on each job.
+ * workspace: at least modexp_mixed_workspace_bytes(jobs, njobs) bytes, 256-byte
+ * aligned (window tables plus the tile counter, which the call resets on `stream`).
+ */
+typedef struct {
+    uint32_t *y;            /* results, n words per instance, context layout */
+    const uint32_t *base;   /* bases < N */
+    const uint32_t *exp;    /* ceil(exp_bits/32) words per instance */
+    uint32_t exp_bits;      /* public exponent length */
+    uint32_t window;        /* 1..6, 0 = tuned */
+    const mont_ctx *ctx;
+} mp_modexp_job;
+size_t modexp_mixed_workspace_bytes(const mp_modexp_job *jobs, int njobs);
+int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_red red, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
+/*
+ * Tuning (process-wide; set it before issuing work, not concurrently with it).
+ * Every operand size maps to a size class (its padded word count); a class has one
+ * or more compiled group shapes: G threads cooperate on one instance, each holding
+ * M words. mp_shape_candidates lists them (default first; returns how many).
+ * mp_tune_set selects the shape (G = M = 0 keeps it), the default window width of
+ * modexp_consttime for window = 0 (0: built-in rule) and the size from which
+ * MP_ALGO_AUTO products use Karatsuba (0: built-in rule) for the class of `bits`.
+ * Contexts stay valid across changes (their layout depends on the class only).
+ */
+int mp_shape_candidates(uint32_t bits, int *G, int *M, int max);
+int mp_tune_set(uint32_t bits, int G, int M, uint32_t window, uint32_t karatsuba_from_bits);
+int mp_tune_get(uint32_t bits, int *G, int *M, uint32_t *window, uint32_t *karatsuba_from_bits);
+
+/*
  * modexp_consttime without any device allocation. The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory on the
  * call path, e.g. a service that reserved its whole memory budget up front, code

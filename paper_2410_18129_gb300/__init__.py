@@ -46,6 +46,11 @@ _SIG = {
     "modexp_consttime": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp, _sz, _vp], _i),
     "mp_bench_imad": ([_i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp], _i),
     "modexp_consttime_noalloc": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp], _i),
+    "mp_shape_candidates": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), _i], _i),
+    "mp_tune_set": ([_u32, _i, _i, _u32, _u32], _i),
+    "mp_tune_get": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i),
+    "modexp_mixed_workspace_bytes": ([_vp, _i], _sz),
+    "modexp_consttime_mixed": ([_vp, _i, _i, _vp, _sz, _vp], _i),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -175,6 +180,60 @@ def modexp_consttime(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("base", ctypes.c_void_p), ("exp", ctypes.c_void_p),
+                ("exp_bits", ctypes.c_uint32), ("window", ctypes.c_uint32), ("ctx", ctypes.c_void_p)]
+
+
+def _jobs(jobs):
+    """jobs: sequence of (y, base, exp, exp_bits, ctx, window) -> ctypes array."""
+    arr = (_Job * len(jobs))()
+    for i, (y, base, exp, exp_bits, ctx, window) in enumerate(jobs):
+        arr[i] = _Job(_ptr(y), _ptr(base), _ptr(exp), exp_bits, window, ctx.handle)
+    return arr
+
+
+def modexp_mixed_workspace_bytes(jobs) -> int:
+    arr = _jobs(jobs)
+    return int(_lib.modexp_mixed_workspace_bytes(arr, len(jobs)))
+
+
+def modexp_consttime_mixed(jobs, red: int = RED_TRUNCATED, workspace: torch.Tensor | None = None):
+    """One persistent launch over several (y, base, exp, exp_bits, ctx, window) jobs."""
+    arr = _jobs(jobs)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.modexp_consttime_mixed(arr, len(jobs), red, _ptr(workspace), ws_bytes, _stream()),
+           "modexp_consttime_mixed")
+
+
+def mixed_workspace(jobs) -> torch.Tensor:
+    """A 256-byte-aligned device buffer large enough for these jobs."""
+    nbytes = modexp_mixed_workspace_bytes(jobs)
+    if nbytes == 0:
+        raise MpError(-1, "modexp_mixed_workspace_bytes")
+    return torch.empty((nbytes + 255) // 256 * 64, dtype=torch.int32, device="cuda")
+
+
+def shape_candidates(bits: int):
+    G = (ctypes.c_int * 8)()
+    M = (ctypes.c_int * 8)()
+    k = _lib.mp_shape_candidates(bits, G, M, 8)
+    if k < 0:
+        raise MpError(k, "mp_shape_candidates")
+    return [(G[i], M[i]) for i in range(min(k, 8))]
+
+
+def tune_set(bits: int, G: int = 0, M: int = 0, window: int = 0, karatsuba_from_bits: int = 0):
+    _check(_lib.mp_tune_set(bits, G, M, window, karatsuba_from_bits), "mp_tune_set")
+
+
+def tune_get(bits: int):
+    G, M, w, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(_lib.mp_tune_get(bits, ctypes.byref(G), ctypes.byref(M), ctypes.byref(w), ctypes.byref(k)),
+           "mp_tune_get")
+    return {"G": G.value, "M": M.value, "window": w.value, "karatsuba_from_bits": k.value}
 
 
 def modexp_consttime_noalloc(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,

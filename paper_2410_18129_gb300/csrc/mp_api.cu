@@ -5,16 +5,19 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include "mp_kernels.cuh"
-#include "../../include/mpgpu.h"
+#include "mp_internal.h"
 
 namespace mpg {
 ShapeOps shape_ops_2_4();
 ShapeOps shape_ops_4_4();
 ShapeOps shape_ops_4_8();
+ShapeOps shape_ops_8_4();
 ShapeOps shape_ops_8_8();
+ShapeOps shape_ops_16_4();
 ShapeOps shape_ops_8_12();
+ShapeOps shape_ops_16_6();
 ShapeOps shape_ops_8_16();
+ShapeOps shape_ops_16_8();
 ShapeOps shape_ops_8_18();
 }  // namespace mpg
 
@@ -26,35 +29,46 @@ static constexpr uint32_t MAX_BITS = 32 * MAX_NP;
 // (266 vs 216 M mul/s) and Karatsuba above it (4108/4154 bits: 214 vs 195 M mul/s)
 static constexpr uint32_t KARATSUBA_FROM_BITS = 4097;
 
-// smallest shape whose padded size holds n words
-static const ShapeOps *shape_for(uint32_t n) {
-    static ShapeOps table[7];
-    static bool init = false;
-    if (!init) {
-        table[0] = shape_ops_2_4();
-        table[1] = shape_ops_4_4();
-        table[2] = shape_ops_4_8();
-        table[3] = shape_ops_8_8();
-        table[4] = shape_ops_8_12();
-        table[5] = shape_ops_8_16();
-        table[6] = shape_ops_8_18();
-        init = true;
-    }
-    for (auto &s : table)
-        if ((uint32_t)s.NP >= n) return &s;
+// Size classes: one per padded size NP. Each class has one or more compiled group
+// shapes (threads per instance x words per thread); the first is the default and
+// mp_tune_set may select another, together with the default window width.
+struct SizeClass {
+    uint32_t np;
+    int nshapes;
+    ShapeOps shapes[2];
+    int chosen;          // index into shapes
+    uint32_t window;     // default window for modexp (0: built-in rule)
+    uint32_t kara_from;  // AUTO products use Karatsuba from this many bits (0: built-in rule)
+};
+static SizeClass g_classes[7];
+static bool g_classes_ready = false;
+
+static void init_classes() {
+    if (g_classes_ready) return;
+    g_classes[0] = SizeClass{8, 1, {shape_ops_2_4()}, 0, 0, 0};
+    g_classes[1] = SizeClass{16, 1, {shape_ops_4_4()}, 0, 0, 0};
+    g_classes[2] = SizeClass{32, 2, {shape_ops_4_8(), shape_ops_8_4()}, 0, 0, 0};
+    g_classes[3] = SizeClass{64, 2, {shape_ops_8_8(), shape_ops_16_4()}, 0, 0, 0};
+    g_classes[4] = SizeClass{96, 2, {shape_ops_8_12(), shape_ops_16_6()}, 0, 0, 0};
+    g_classes[5] = SizeClass{128, 2, {shape_ops_16_8(), shape_ops_8_16()}, 0, 0, 0};   // 16x8 measured faster
+    g_classes[6] = SizeClass{144, 1, {shape_ops_8_18()}, 0, 0, 0};
+    g_classes_ready = true;
+}
+
+static SizeClass *class_for(uint32_t n) {
+    init_classes();
+    for (auto &c : g_classes)
+        if (c.np >= n) return &c;
     return nullptr;
 }
 
-struct mont_ctx {
-    size_t batch;
-    uint32_t bits, n, np;
-    mp_layout layout;
-    const ShapeOps *shape;
-    uint32_t *mem;            // one allocation for everything below
-    uint32_t *N, *NI, *R1, *R2, *K;           // internal: interleaved, np words
-    uint32_t *NI_api, *R1_api, *R2_api, *N_api;  // API layout, n words
-    size_t api_words;         // words of one API array
-};
+// the selected shape for operands of n words
+static const ShapeOps *shape_for(uint32_t n) {
+    SizeClass *c = class_for(n);
+    return c ? &c->shapes[c->chosen] : nullptr;
+}
+
+
 
 static inline uint32_t words_for(uint32_t bits) { return (bits + 31u) / 32u; }
 static inline size_t api_array_words(mp_layout layout, size_t batch, uint32_t words) {
@@ -150,7 +164,9 @@ static int product(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t bat
     KArgs A{};
     A.out = c; A.a = a; A.b = square ? a : b;
     A.batch = batch; A.n = (int)n; A.layout = (int)layout; A.square = square ? 1 : 0;
-    bool kara = algo == MP_ALGO_KARATSUBA || (algo == MP_ALGO_AUTO && bits >= KARATSUBA_FROM_BITS);
+    const SizeClass *cls = class_for(n);
+    const uint32_t kfrom = cls->kara_from ? cls->kara_from : KARATSUBA_FROM_BITS;
+    bool kara = algo == MP_ALGO_KARATSUBA || (algo == MP_ALGO_AUTO && bits >= kfrom);
     if (kara && !sh->kara) {
         if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
         kara = false;
@@ -258,7 +274,7 @@ extern "C" int mont_ctx_init(mont_ctx **out, const uint32_t *N, size_t batch, ui
     if (!sh) return MP_ERR_SIZE;
     mont_ctx *c = new (std::nothrow) mont_ctx{};
     if (!c) return MP_ERR_NOMEM;
-    c->batch = batch; c->bits = bits; c->n = n; c->np = (uint32_t)sh->NP; c->layout = layout; c->shape = sh;
+    c->batch = batch; c->bits = bits; c->n = n; c->np = (uint32_t)sh->NP; c->layout = layout;
     c->api_words = api_array_words(layout, batch, n);
     const size_t internal = (size_t)c->np * batch;
     const size_t total = 5 * internal + 4 * c->api_words + 4;   // +4: the error word (8 bytes, kept aligned)
@@ -338,6 +354,8 @@ static void fill_ctx_args(KArgs &A, const mont_ctx *c) {
     A.correct = (c->n != c->np) ? 1 : 0;
 }
 
+void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }
+
 static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
                        mp_algo algo, bool square, void *stream) {
     if (!out || !a || (!square && !b) || !c) return MP_ERR_ARG;
@@ -349,7 +367,7 @@ static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, cons
     KArgs A{};
     fill_ctx_args(A, c);
     A.out = out; A.a = a; A.b = square ? a : b; A.red = (int)red; A.square = square ? 1 : 0;
-    return cuda_status(c->shape->mont(A, S(stream)));
+    return cuda_status(shape_for(c->np)->mont(A, S(stream)));
 }
 
 extern "C" int mont_mul(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
@@ -364,7 +382,52 @@ extern "C" int mont_sqr(uint32_t *out, const uint32_t *a, const mont_ctx *c, mp_
 
 // ------------------------------------------------------------------ exponentiation
 
-static uint32_t tuned_window(uint32_t bits) { return bits <= 1024 ? 4u : bits <= 3072 ? 5u : 6u; }
+// window for window = 0: the tuned one for the size class, else 4 up to 1024 bits,
+// 5 up to 3072, 6 above (Sec. 6.4 found 4 best at 1024 bits and 5 above)
+static uint32_t tuned_window(uint32_t bits) {
+    const SizeClass *c = class_for(words_for(bits));
+    if (c && c->window) return c->window;
+    return bits <= 1024 ? 4u : bits <= 3072 ? 5u : 6u;
+}
+
+uint32_t mpg::default_window(uint32_t bits) { return tuned_window(bits); }
+
+extern "C" int mp_shape_candidates(uint32_t bits, int *G, int *M, int max) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    const SizeClass *c = class_for(words_for(bits));
+    int k = 0;
+    for (int i = 0; i < c->nshapes && k < max; ++i, ++k) {
+        if (G) G[k] = c->shapes[i].G;
+        if (M) M[k] = c->shapes[i].M;
+    }
+    return c->nshapes;
+}
+
+extern "C" int mp_tune_set(uint32_t bits, int G, int M, uint32_t window, uint32_t karatsuba_from_bits) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (window > 6) return MP_ERR_SIZE;
+    SizeClass *c = class_for(words_for(bits));
+    int pick = -1;
+    for (int i = 0; i < c->nshapes; ++i)
+        if (c->shapes[i].G == G && c->shapes[i].M == M) pick = i;
+    if (G != 0 || M != 0) {
+        if (pick < 0) return MP_ERR_ARG;
+        c->chosen = pick;
+    }
+    c->window = window;
+    c->kara_from = karatsuba_from_bits;
+    return MP_OK;
+}
+
+extern "C" int mp_tune_get(uint32_t bits, int *G, int *M, uint32_t *window, uint32_t *karatsuba_from_bits) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    const SizeClass *c = class_for(words_for(bits));
+    if (G) *G = c->shapes[c->chosen].G;
+    if (M) *M = c->shapes[c->chosen].M;
+    if (window) *window = tuned_window(bits);
+    if (karatsuba_from_bits) *karatsuba_from_bits = c->kara_from ? c->kara_from : KARATSUBA_FROM_BITS;
+    return MP_OK;
+}
 
 extern "C" size_t modexp_workspace_bytes(size_t batch, uint32_t bits, uint32_t window) {
     if (bits == 0 || bits > MAX_BITS) return 0;
@@ -405,7 +468,7 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     A.out = y; A.a = base; A.e = exp; A.table = reinterpret_cast<uint32_t *>(ws);
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
-    int rc = cuda_status(c->shape->modexp(A, st));
+    int rc = cuda_status(shape_for(c->np)->modexp(A, st));
     if (own) {
         if (cudaFreeAsync(ws, st) != cudaSuccess && rc == MP_OK) rc = MP_ERR_CUDA;
     }
@@ -464,5 +527,5 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
     A.out = y; A.a = base; A.e = exp; A.table = tables;
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
-    return cuda_status(c->shape->modexp(A, S(stream)));
+    return cuda_status(shape_for(c->np)->modexp(A, S(stream)));
 }

@@ -187,12 +187,11 @@ MPG_DI uint32_t window_bits(const KArgs &A, size_t k, bool valid, int pos, int w
     return v;
 }
 
-template <class S, int TPB, int RED>
-__global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
+// One group's constant-time exponentiation of instance k (Alg. 7). Shared by the
+// one-size kernel and the mixed-size persistent kernel.
+template <class S, int RED>
+MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     constexpr int M = S::M, NP = S::NP;
-    extern __shared__ uint4 smem4[];
-    Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
-    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
     const bool valid = k < A.batch;
     const int w = A.window;
     const int E = 1 << w;
@@ -298,6 +297,14 @@ __global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
     lds<M>(x, g.X() + g.t * M);
     gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
     (void)NP;
+}
+
+template <class S, int TPB, int RED>
+__global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
+    extern __shared__ uint4 smem4[];
+    Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
+    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    modexp_group<S, RED>(g, A, k);
 }
 
 // ------------------------------------------------------------------ per-shape launch table

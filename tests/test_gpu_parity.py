@@ -292,3 +292,72 @@ def test_karatsuba_auto_and_small_sizes(mp):
         mp.mp_mul(out_tensor(mp, 4, 16, IM), dev(mp, small, IM), dev(mp, small, IM), 4, 256, IM,
                   mp.ALGO_KARATSUBA)
     assert e.value.status == -7
+
+
+# ------------------------------------------------------------------ mixed sizes, one persistent launch
+
+def _mixed_jobs(mp, specs, layout):
+    jobs, batches, outs = [], [], []
+    for bits, batch, ebits, window, sub in specs:
+        b = si.make_batch(0, "mixed", batch, bits, ebits=ebits, sub=sub)
+        ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
+        Y = out_tensor(mp, batch, b.n, layout)
+        jobs.append((Y, dev(mp, b.a, layout), dev(mp, b.e, layout), ebits, ctx, window))
+        batches.append(b)
+        outs.append(Y)
+    return jobs, batches, outs
+
+
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_mixed_persistent_matches_per_size(mp, layout):
+    specs = [(2048, 70, 2048, 5, 1), (1024, 133, 1024, 4, 2), (3072, 21, 3072, 5, 3), (4096, 17, 4096, 6, 4),
+             (512, 40, 300, 3, 5), (1000, 9, 64, 0, 6)]
+    jobs, batches, outs = _mixed_jobs(mp, specs, layout)
+    ws = mp.mixed_workspace(jobs)
+    for red in (0, 1):
+        for Y in outs:
+            Y.zero_()
+        mp.modexp_consttime_mixed(jobs, red, ws)
+        torch.cuda.synchronize()
+        for (Y, A, E, ebits, ctx, window), b in zip(jobs, batches):
+            Z = torch.zeros_like(Y)
+            mp.modexp_consttime(Z, A, E, ebits, ctx, window, red)
+            got = host(mp, Y, b.batch, b.n, layout)
+            assert_equal(got, host(mp, Z, b.batch, b.n, layout), f"mixed vs one-size {b.bits}")
+            idx = np.arange(0, b.batch, max(1, b.batch // 5))
+            want = oracle.modexp(b.a[idx], b.e[idx], ebits, b.N[idx])
+            assert_equal(got[idx], want, f"mixed vs oracle {b.bits}")
+
+
+def test_mixed_rejects_unsupported(mp):
+    """Sizes above 4096 bits have no shape in the persistent kernel: rejected before any launch."""
+    b = si.make_batch(0, "mixed", 4, 4108, ebits=8, sub=9)
+    ctx = mp.MontCtx(dev(mp, b.N, IM), 4, 4108, IM)
+    Y = out_tensor(mp, 4, b.n, IM)
+    job = [(Y, dev(mp, b.a, IM), dev(mp, b.e, IM), 8, ctx, 5)]
+    assert mp.modexp_mixed_workspace_bytes(job) == 0
+    ws = torch.empty(1 << 20, dtype=torch.int32, device="cuda")
+    with pytest.raises(mp.MpError) as e:
+        mp.modexp_consttime_mixed(job, 0, ws)
+    assert e.value.status == -7
+
+
+def test_tuning_round_trip(mp):
+    for bits in (1024, 2048, 3072, 4096):
+        cands = mp.shape_candidates(bits)
+        assert len(cands) >= 1
+        before = mp.tune_get(bits)
+        for G, M in cands:
+            mp.tune_set(bits, G, M, 4)
+            t = mp.tune_get(bits)
+            assert (t["G"], t["M"], t["window"]) == (G, M, 4)
+            # results do not depend on the shape
+            b = si.make_batch(0, "test", 12, bits, ebits=96, sub=bits + G)
+            ctx = mp.MontCtx(dev(mp, b.N, IL), 12, bits, IL)
+            Y = out_tensor(mp, 12, b.n, IL)
+            mp.modexp_consttime(Y, dev(mp, b.a, IL), dev(mp, b.e, IL), 96, ctx, 0)
+            assert_equal(host(mp, Y, 12, b.n, IL), oracle.modexp(b.a, b.e, 96, b.N), f"shape {G}x{M}")
+            C = out_tensor(mp, 12, b.n, IL)
+            mp.mont_mul(C, dev(mp, b.a, IL), dev(mp, b.b, IL), ctx)
+            assert_equal(host(mp, C, 12, b.n, IL), oracle.mont_def(b.a, b.b, b.N), f"mont shape {G}x{M}")
+        mp.tune_set(bits, before["G"], before["M"], 0)
