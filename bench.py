@@ -132,7 +132,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--quick", action="store_true",
                     help="time the modexp steps only (no comparison runs, no e2e, no CPU baseline): for profiling")
-    ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096", "mixed"],
+    ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096", "mixed", "serving"],
                     help="batch_2048: the headline line; batch_4096: 4096-bit products (schoolbook vs "
                          "Karatsuba, 4108/4154 edges), Montgomery and w=6 modexp")
     args = ap.parse_args()
@@ -140,6 +140,8 @@ def main():
         return bench_4096(args)
     if args.workload == "mixed":
         return bench_mixed(args)
+    if args.workload == "serving":
+        return bench_serving(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -522,6 +524,50 @@ def bench_mixed(args):
     print(json.dumps(line))
     for c in ctxs:
         c.free()
+
+
+def bench_serving(args):
+    """Serving: Poisson arrivals at 1e4..1e6 req/s over a resident pool of 4096 moduli (mixed
+    sizes, fixed bases, tables on the device). Each rate is replayed through the continuous-
+    batching loop (4 streams, one persistent launch per batch, admission by device memory) and
+    through the plain path (one batch at a time, one launch per size). Reports p50/p99 latency
+    and throughput per rate; `value` is the continuous loop's throughput at the highest rate."""
+    import seeded_inputs as si
+    import torch
+    import paper_2410_18129_gb300 as mp
+    from paper_2410_18129_gb300 import serve as sv
+    from paper_2410_18129_gb300 import tune
+
+    torch.cuda.set_device(0)
+    choice = tune.load_or_tune(sizes=(1024, 2048, 3072, 4096))
+    rates = (1e4, 3e4, 1e5, 3e5, 1e6)
+    seconds = 4.0
+    cap = 100000 if args.batch == 65536 else args.batch
+    pool = sv.Pool(mp, seed=0, count=4096)
+    traces = {r: si.poisson_trace(0, r, int(min(r * seconds, cap)), pool.sizes) for r in rates}
+    free = torch.cuda.mem_get_info()[0]
+    out = {}
+    with ClockSampler(0) as clk:
+        for r in rates:
+            tr = traces[r]
+            adm = sv.AdmissionController(free_fn=lambda: free, fraction=0.5, reserve=1 << 30)
+            cont = sv.serve(tr, sv.ContinuousExecutor(pool, tr, slots=4), slots=4, max_batch=16384, admission=adm)
+            plain = sv.serve(tr, sv.PlainExecutor(pool, tr), slots=1, max_batch=16384)
+            out[f"{r:.0e}"] = {"offered_per_s": r, "continuous": cont.summary(), "plain": plain.summary()}
+    top = out[f"{rates[-1]:.0e}"]["continuous"]
+    line = {
+        "metric": "serving: p50/p99 latency and throughput under Poisson load (mixed sizes, resident moduli)",
+        "value": top["throughput_per_s"], "unit": "modexp/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "serving: pool of 4096 moduli (1639 x 2048, 1024 x 1024, 819 x 3072, 614 x 4096 "
+                               "bits), fixed base per modulus with resident tables, full-length exponents, "
+                               f"Poisson arrivals, up to {seconds:.0f} s or {cap} requests per rate",
+                   "windows": {b: c["window"] for b, c in choice.items()}, "slots": 4, "max_batch": 16384},
+        "rates": out, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    pool.free()
 
 
 if __name__ == "__main__":

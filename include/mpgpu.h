@@ -161,15 +161,40 @@ int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uin
  */
 typedef struct {
     uint32_t *y;            /* results, n words per instance, context layout */
-    const uint32_t *base;   /* bases < N */
+    const uint32_t *base;   /* bases < N (unused for fixed-base jobs) */
     const uint32_t *exp;    /* ceil(exp_bits/32) words per instance */
     uint32_t exp_bits;      /* public exponent length */
-    uint32_t window;        /* 1..6, 0 = tuned */
+    uint32_t window;        /* 1..6, 0 = tuned (fixed-base jobs: the tables' window) */
     const mont_ctx *ctx;
+    /* fixed-base job when index != NULL: nreq requests, request i uses context instance
+       index[i] and its resident table in `tables` (see modexp_table_build); y and exp then
+       hold nreq instances */
+    const uint32_t *index;
+    const void *tables;
+    size_t nreq;
 } mp_modexp_job;
 size_t modexp_mixed_workspace_bytes(const mp_modexp_job *jobs, int njobs);
 int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_red red, void *workspace,
                            size_t workspace_bytes, void *stream);
+
+/*
+ * Resident window tables for fixed bases (serving: each modulus of a pool keeps its
+ * base's table on the device, so a request costs only the window loop of Alg. 7).
+ * modexp_table_bytes: device bytes of the tables of every instance of ctx at width
+ * `window` (1..6). modexp_table_build: tables[k] = base_k^i * R mod N_k, i < 2^window,
+ * for every instance k of ctx (base in the context layout).
+ * modexp_fixed_base: y_i = base_{index[i]}^{e_i} mod N_{index[i]} for nreq requests;
+ * index: nreq words (instance numbers < batch of ctx); y and exp: nreq instances in
+ * the context layout; `window` must be the one the tables were built with. The same
+ * constant-time window loop and masked scan as modexp_consttime; index values are
+ * public routing data. Out-of-range indexes leave their outputs unwritten.
+ */
+size_t modexp_table_bytes(const mont_ctx *ctx, uint32_t window);
+int modexp_table_build(void *tables, size_t bytes, const uint32_t *base, const mont_ctx *ctx,
+                       uint32_t window, mp_red red, void *stream);
+int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint32_t *exp, uint32_t exp_bits,
+                      size_t nreq, const mont_ctx *ctx, const void *tables, uint32_t window, mp_red red,
+                      void *stream);
 
 /*
  * Tuning (process-wide; set it before issuing work, not concurrently with it).

@@ -51,6 +51,9 @@ _SIG = {
     "mp_tune_get": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i),
     "modexp_mixed_workspace_bytes": ([_vp, _i], _sz),
     "modexp_consttime_mixed": ([_vp, _i, _i, _vp, _sz, _vp], _i),
+    "modexp_table_bytes": ([_vp, _u32], _sz),
+    "modexp_table_build": ([_vp, _sz, _vp, _vp, _u32, _i, _vp], _i),
+    "modexp_fixed_base": ([_vp, _vp, _vp, _u32, _sz, _vp, _vp, _u32, _i, _vp], _i),
 }
 for _name, (_args, _res) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -184,15 +187,40 @@ NOALLOC_SCRATCH_BYTES = 16 << 20
 
 class _Job(ctypes.Structure):
     _fields_ = [("y", ctypes.c_void_p), ("base", ctypes.c_void_p), ("exp", ctypes.c_void_p),
-                ("exp_bits", ctypes.c_uint32), ("window", ctypes.c_uint32), ("ctx", ctypes.c_void_p)]
+                ("exp_bits", ctypes.c_uint32), ("window", ctypes.c_uint32), ("ctx", ctypes.c_void_p),
+                ("index", ctypes.c_void_p), ("tables", ctypes.c_void_p), ("nreq", ctypes.c_size_t)]
 
 
 def _jobs(jobs):
-    """jobs: sequence of (y, base, exp, exp_bits, ctx, window) -> ctypes array."""
+    """jobs: sequence of (y, base, exp, exp_bits, ctx, window) for exponentiations of a
+    context's own bases, or (y, None, exp, exp_bits, ctx, window, index, tables, nreq) for
+    fixed-base requests on resident tables -> ctypes array."""
     arr = (_Job * len(jobs))()
-    for i, (y, base, exp, exp_bits, ctx, window) in enumerate(jobs):
-        arr[i] = _Job(_ptr(y), _ptr(base), _ptr(exp), exp_bits, window, ctx.handle)
+    for i, job in enumerate(jobs):
+        y, base, exp, exp_bits, ctx, window = job[:6]
+        if len(job) > 6:
+            index, tables, nreq = job[6:9]
+            arr[i] = _Job(_ptr(y), None, _ptr(exp), exp_bits, window, ctx.handle, _ptr(index), _ptr(tables), nreq)
+        else:
+            arr[i] = _Job(_ptr(y), _ptr(base), _ptr(exp), exp_bits, window, ctx.handle, None, None, 0)
     return arr
+
+
+def modexp_table_bytes(ctx: MontCtx, window: int) -> int:
+    return int(_lib.modexp_table_bytes(ctx.handle, window))
+
+
+def modexp_table_build(tables: torch.Tensor, base, ctx: MontCtx, window: int, red: int = RED_TRUNCATED):
+    _check(_lib.modexp_table_build(_ptr(tables), tables.numel() * tables.element_size(), _ptr(base), ctx.handle,
+                                   window, red, _stream()), "modexp_table_build")
+    return tables
+
+
+def modexp_fixed_base(y, index, exp, exp_bits: int, nreq: int, ctx: MontCtx, tables: torch.Tensor, window: int,
+                      red: int = RED_TRUNCATED):
+    _check(_lib.modexp_fixed_base(_ptr(y), _ptr(index), _ptr(exp), exp_bits, nreq, ctx.handle, _ptr(tables),
+                                  window, red, _stream()), "modexp_fixed_base")
+    return y
 
 
 def modexp_mixed_workspace_bytes(jobs) -> int:

@@ -163,15 +163,18 @@ static int product(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t bat
     if (!sh) return MP_ERR_SIZE;
     KArgs A{};
     A.out = c; A.a = a; A.b = square ? a : b;
-    A.batch = batch; A.n = (int)n; A.layout = (int)layout; A.square = square ? 1 : 0;
+    A.batch = batch; A.cbatch = batch; A.n = (int)n; A.layout = (int)layout; A.square = square ? 1 : 0;
     const SizeClass *cls = class_for(n);
     const uint32_t kfrom = cls->kara_from ? cls->kara_from : KARATSUBA_FROM_BITS;
     bool kara = algo == MP_ALGO_KARATSUBA || (algo == MP_ALGO_AUTO && bits >= kfrom);
-    if (kara && !sh->kara) {
+    const ShapeOps *ksh = sh->kara ? sh : nullptr;   // any shape of the class with a Karatsuba kernel
+    for (int i = 0; i < cls->nshapes && !ksh; ++i)
+        if (cls->shapes[i].kara) ksh = &cls->shapes[i];
+    if (kara && !ksh) {
         if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
         kara = false;
     }
-    return cuda_status(kara ? sh->kara(A, S(stream)) : sh->mul(A, S(stream)));
+    return cuda_status(kara ? ksh->kara(A, S(stream)) : sh->mul(A, S(stream)));
 }
 
 extern "C" int mp_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,
@@ -350,8 +353,10 @@ extern "C" int mont_ctx_export(const mont_ctx *c, int which, uint32_t *dst, void
 
 static void fill_ctx_args(KArgs &A, const mont_ctx *c) {
     A.N = c->N; A.NI = c->NI; A.R1 = c->R1; A.R2 = c->R2; A.K = c->K;
-    A.batch = c->batch; A.n = (int)c->n; A.layout = (int)c->layout;
+    A.batch = c->batch; A.cbatch = c->batch; A.n = (int)c->n; A.layout = (int)c->layout;
     A.correct = (c->n != c->np) ? 1 : 0;
+    A.index = nullptr;
+    A.mode = 0;
 }
 
 void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }
@@ -473,6 +478,45 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
         if (cudaFreeAsync(ws, st) != cudaSuccess && rc == MP_OK) rc = MP_ERR_CUDA;
     }
     return rc;
+}
+
+// ------------------------------------------------------------------ resident tables, fixed bases
+
+extern "C" size_t modexp_table_bytes(const mont_ctx *c, uint32_t window) {
+    if (!c || window == 0 || window > 6) return 0;
+    return ((size_t)1 << window) * (size_t)c->np * c->batch * 4;
+}
+
+extern "C" int modexp_table_build(void *tables, size_t bytes, const uint32_t *base, const mont_ctx *c,
+                                  uint32_t window, mp_red red, void *stream) {
+    if (!tables || !base || !c) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (window == 0 || window > 6) return MP_ERR_SIZE;
+    if (!aligned16(tables) || (c->layout == MP_LAYOUT_INTERLEAVED && !aligned16(base))) return MP_ERR_ALIGN;
+    if (bytes < modexp_table_bytes(c, window)) return MP_ERR_NOMEM;
+    KArgs A{};
+    fill_ctx_args(A, c);
+    A.a = base; A.table = reinterpret_cast<uint32_t *>(tables); A.window = (int)window; A.red = (int)red;
+    A.mode = 1;
+    return cuda_status(shape_for(c->np)->modexp(A, S(stream)));
+}
+
+extern "C" int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint32_t *exp, uint32_t exp_bits,
+                                 size_t nreq, const mont_ctx *c, const void *tables, uint32_t window, mp_red red,
+                                 void *stream) {
+    if (!y || !index || !c || !tables || (exp_bits > 0 && !exp) || nreq == 0) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (window == 0 || window > 6) return MP_ERR_SIZE;
+    if (!aligned16(tables) || (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || (exp && !aligned16(exp)))))
+        return MP_ERR_ALIGN;
+    KArgs A{};
+    fill_ctx_args(A, c);
+    A.out = y; A.e = exp; A.index = index; A.batch = nreq;
+    A.table = const_cast<uint32_t *>(reinterpret_cast<const uint32_t *>(tables));
+    A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
+    A.red = (int)red;
+    A.mode = 2;
+    return cuda_status(shape_for(c->np)->modexp(A, S(stream)));
 }
 
 // ------------------------------------------------------------------ exponentiation without allocation

@@ -81,11 +81,14 @@ struct KArgs {
     const uint32_t *R1;
     const uint32_t *R2;
     const uint32_t *K;
-    uint32_t *table;         // window tables: [entry][NP/4][batch] uint4
-    size_t batch;
+    uint32_t *table;         // window tables: [entry][NP/4][cbatch] uint4
+    size_t batch;            // instances of the API arrays (requests)
     int n;                   // API words per value
     int layout;              // API layout
     int ebits, ne, window, red, square, correct;
+    const uint32_t *index;   // fixed-base requests: request k uses context instance index[k]
+    size_t cbatch;           // instances of the context arrays and tables (== batch without index)
+    int mode;                // exponentiation: 0 build the table and run, 1 build only, 2 run on a resident table
 };
 
 template <class S>
@@ -119,7 +122,7 @@ MPG_DI void load_api(const Grp<S> &g, uint32_t *dst, const uint32_t *src, const 
 template <class S>
 MPG_DI void load_ctx(const Grp<S> &g, uint32_t *dst, const uint32_t *src, const KArgs &A, size_t k, bool valid) {
     uint32_t x[S::M];
-    gload<S::M>(x, src, LAYOUT_IL, k, valid, g.t * S::M, S::NP, A.batch);
+    gload<S::M>(x, src, LAYOUT_IL, k, valid, g.t * S::M, S::NP, A.cbatch);
     sts<S::M>(dst + g.t * S::M, x);
 }
 
@@ -187,72 +190,79 @@ MPG_DI uint32_t window_bits(const KArgs &A, size_t k, bool valid, int pos, int w
     return v;
 }
 
-// One group's constant-time exponentiation of instance k (Alg. 7). Shared by the
-// one-size kernel and the mixed-size persistent kernel.
+// One group's constant-time exponentiation (Alg. 7) of request k. Request k uses
+// context instance kc = index[k] (fixed-base requests on a resident pool) or k.
+// Shared by the one-size kernel and the mixed-size persistent kernel.
+//   mode 0: build the window table of base k, then run the windows
+//   mode 1: only build the table (a resident table for later fixed-base requests)
+//   mode 2: run the windows on the resident table of instance kc
 template <class S, int RED>
 MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
-    constexpr int M = S::M, NP = S::NP;
-    const bool valid = k < A.batch;
+    constexpr int M = S::M;
+    bool valid = k < A.batch;
+    const size_t kc = (A.index && valid) ? (size_t)A.index[k] : k;   // routing: public
+    valid = valid && kc < A.cbatch;
     const int w = A.window;
     const int E = 1 << w;
-    const size_t batch = A.batch;
+    const size_t cb = A.cbatch;
     uint4 *tab = reinterpret_cast<uint4 *>(A.table);
-    static_assert(M % 4 == 0 || M % 2 == 0, "");
 
-    auto put = [&](int e, const uint32_t *src) {
+    auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
         uint32_t x[M];
         lds<M>(x, src + g.t * M);
         if (!valid) return;
         if constexpr (M % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c)
-                tab[tidx4<S>(e, g.t * (M / 4) + c, k, batch)] =
+                tab[tidx4<S>(e, g.t * (M / 4) + c, kc, cb)] =
                     make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
         } else {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = g.t * M + j;
-                A.table[tidx4<S>(e, i >> 2, k, batch) * 4 + (i & 3)] = x[j];
+                A.table[tidx4<S>(e, i >> 2, kc, cb) * 4 + (i & 3)] = x[j];
             }
         }
     };
-
-    auto get = [&](int e, uint32_t *dst) {   // this thread's M words of table entry e
-        uint32_t x[M];
+    auto fetch = [&](int e, uint32_t (&x)[M]) {     // table entry e -> this thread's M words
         if constexpr (M % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c) {
                 uint4 v = make_uint4(0, 0, 0, 0);
-                if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, k, batch)];
+                if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, kc, cb)];
                 x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = g.t * M + j;
-                x[j] = valid ? A.table[tidx4<S>(e, i >> 2, k, batch) * 4 + (i & 3)] : 0u;
+                x[j] = valid ? A.table[tidx4<S>(e, i >> 2, kc, cb) * 4 + (i & 3)] : 0u;
             }
         }
-        sts<M>(dst + g.t * M, x);
     };
 
     init_zero_block<S>(g);
-    load_ctx<S>(g, g.N(), A.N, A, k, valid);
-    load_ctx<S>(g, g.NI(), A.NI, A, k, valid);
-    load_api<S>(g, g.X(), A.a, A, k, valid);
-    load_ctx<S>(g, g.Y(), A.R2, A, k, valid);
-    gsync();
-    mont_mul<S, RED>(g, false);                 // X = a*R mod N = G[1]
-    put(1, g.X());
-    load_ctx<S>(g, g.Y(), A.R1, A, k, valid);     // G[0] = R mod N
-    put(0, g.Y());
-    for (int e = 2; e < E; ++e) {                 // G[e] = G[e-1] * G[1]
-        get(1, g.Y());                            // (the product leaves q in Y)
+    load_ctx<S>(g, g.N(), A.N, A, kc, valid);
+    load_ctx<S>(g, g.NI(), A.NI, A, kc, valid);
+    if (A.mode != 2) {
+        load_api<S>(g, g.X(), A.a, A, kc, valid);
+        load_ctx<S>(g, g.Y(), A.R2, A, kc, valid);
         gsync();
-        mont_mul<S, RED>(g, false);
-        put(e, g.X());
+        mont_mul<S, RED>(g, false);                 // X = a*R mod N = G[1]
+        put(1, g.X());
+        load_ctx<S>(g, g.Y(), A.R1, A, kc, valid);    // G[0] = R mod N
+        put(0, g.Y());
+        for (int e = 2; e < E; ++e) {                 // G[e] = G[e-1] * G[1]
+            uint32_t x[M];
+            fetch(1, x);                              // (the product leaves q in Y)
+            sts<M>(g.Y() + g.t * M, x);
+            gsync();
+            mont_mul<S, RED>(g, false);
+            put(e, g.X());
+        }
+        if (A.mode == 1) return;
     }
-    load_ctx<S>(g, g.X(), A.R1, A, k, valid);     // Y_acc = 1 in Montgomery form
+    load_ctx<S>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form
     gsync();
     const int windows = (A.ebits + w - 1) / w;
     for (int win = windows - 1; win >= 0; --win) {
@@ -264,20 +274,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
         for (int e = 0; e < E; ++e) {
             const uint32_t m = mask_if_equal((uint32_t)e, bsel);
             uint32_t x[M];
-            if constexpr (M % 4 == 0) {
-#pragma unroll
-                for (int c = 0; c < M / 4; ++c) {
-                    uint4 v = make_uint4(0, 0, 0, 0);
-                    if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, k, batch)];
-                    x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    const int i = g.t * M + j;
-                    x[j] = valid ? A.table[tidx4<S>(e, i >> 2, k, batch) * 4 + (i & 3)] : 0u;
-                }
-            }
+            fetch(e, x);
 #pragma unroll
             for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
         }
@@ -296,7 +293,6 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     uint32_t x[M];
     lds<M>(x, g.X() + g.t * M);
     gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
-    (void)NP;
 }
 
 template <class S, int TPB, int RED>

@@ -106,9 +106,12 @@ static int mix_shape_for(const mont_ctx *c, int *G) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t job_table_bytes(const mp_modexp_job &j) {
+    if (j.index) return 0;   // fixed-base job: resident tables
     const uint32_t w = j.window ? j.window : default_window(j.ctx->bits);
     return ((size_t)1 << w) * (size_t)j.ctx->np * j.ctx->batch * 4;
 }
+
+static size_t job_instances(const mp_modexp_job &j) { return j.index ? j.nreq : j.ctx->batch; }
 
 template <int RED>
 static cudaError_t launch_mixed(const MixArgs &P, cudaStream_t st) {
@@ -139,8 +142,10 @@ static int check_jobs(const mp_modexp_job *jobs, int njobs) {
     if (njobs > MIX_MAX_JOBS) return MP_ERR_SIZE;
     for (int i = 0; i < njobs; ++i) {
         const mp_modexp_job &j = jobs[i];
-        if (!j.y || !j.base || !j.ctx || (j.exp_bits > 0 && !j.exp)) return MP_ERR_ARG;
+        if (!j.y || !j.ctx || (j.exp_bits > 0 && !j.exp)) return MP_ERR_ARG;
+        if (j.index ? (!j.tables || j.nreq == 0 || j.window == 0) : !j.base) return MP_ERR_ARG;
         if (j.window > 6) return MP_ERR_SIZE;
+        if (j.index && ((uintptr_t)j.tables & 15u)) return MP_ERR_ALIGN;
         int G = 0;
         if (mix_shape_for(j.ctx, &G) < 0) return MP_ERR_UNIMPLEMENTED;
         if (j.ctx->layout == MP_LAYOUT_INTERLEAVED &&
@@ -168,8 +173,8 @@ extern "C" int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_r
     int order[MIX_MAX_JOBS];
     for (int i = 0; i < njobs; ++i) order[i] = i;
     std::stable_sort(order, order + njobs, [&](int x, int y) {
-        const double cx = (double)jobs[x].ctx->np * jobs[x].ctx->np * (jobs[x].exp_bits + 1);
-        const double cy = (double)jobs[y].ctx->np * jobs[y].ctx->np * (jobs[y].exp_bits + 1);
+        const double cx = (double)jobs[x].ctx->np * jobs[x].ctx->np * (jobs[x].exp_bits + 64);
+        const double cy = (double)jobs[y].ctx->np * jobs[y].ctx->np * (jobs[y].exp_bits + 64);
         return cx > cy;
     });
     MixArgs P{};
@@ -188,13 +193,20 @@ extern "C" int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_r
         J.A.ne = j.exp_bits ? (int)((j.exp_bits + 31) / 32) : 1;
         J.A.window = (int)(j.window ? j.window : default_window(j.ctx->bits));
         J.A.red = (int)red;
-        J.A.table = reinterpret_cast<uint32_t *>(ws + off);
-        off += align256(job_table_bytes(j));
+        if (j.index) {   // fixed-base requests on resident tables
+            J.A.index = j.index;
+            J.A.batch = j.nreq;
+            J.A.table = const_cast<uint32_t *>(reinterpret_cast<const uint32_t *>(j.tables));
+            J.A.mode = 2;
+        } else {
+            J.A.table = reinterpret_cast<uint32_t *>(ws + off);
+            off += align256(job_table_bytes(j));
+        }
         int G = 0;
         J.shape = mix_shape_for(j.ctx, &G);
         const int gpb = MIX_TPB / G;
         J.tile0 = tile;
-        tile += (int)((j.ctx->batch + gpb - 1) / gpb);
+        tile += (int)((job_instances(j) + gpb - 1) / gpb);
     }
     P.njobs = njobs;
     P.total = tile;

@@ -273,3 +273,35 @@ def mixed_sizes(seed: int, count: int) -> np.ndarray:
     sizes = np.concatenate([np.full(c, b, dtype=np.int32) for (b, _), c in zip(MIX, counts)])
     stream(seed, "mixed", "size").shuffle(sizes)
     return sizes
+
+
+# ----------------------------------------------------------------------------- serving traces
+
+
+@dataclass
+class Trace:
+    """A request trace: arrival times (s, increasing), the pool entry each request uses,
+    and its exponent words (full length for that entry's size, instance-major)."""
+    arrival: np.ndarray      # float64 [count]
+    entry: np.ndarray        # int64 [count], index into the pool
+    exponents: list          # per request: uint32 words
+
+
+def pool_sizes(seed: int, count: int) -> np.ndarray:
+    """Bit sizes of a resident pool of ``count`` moduli with the mixed-size distribution."""
+    return mixed_sizes(seed + 1000, count)
+
+
+def poisson_trace(seed: int, rate: float, count: int, sizes: np.ndarray) -> Trace:
+    """``count`` requests with exponential inter-arrival gaps of mean 1/rate, each picking a
+    pool entry uniformly and carrying a fresh full-length exponent for that entry's size."""
+    r = stream(seed, "serving", "arrival", int(rate))
+    gaps = r.exponential(1.0 / rate, size=count)
+    arrival = np.cumsum(gaps)
+    entry = r.integers(0, len(sizes), size=count)
+    re = stream(seed, "serving", "exponent", int(rate))
+    exps = []
+    for k in entry:
+        bits = int(sizes[k])
+        exps.append(random_bits(re, 1, bits)[0])
+    return Trace(arrival, entry, exps)

@@ -361,3 +361,37 @@ def test_tuning_round_trip(mp):
             mp.mont_mul(C, dev(mp, b.a, IL), dev(mp, b.b, IL), ctx)
             assert_equal(host(mp, C, 12, b.n, IL), oracle.mont_def(b.a, b.b, b.N), f"mont shape {G}x{M}")
         mp.tune_set(bits, before["G"], before["M"], 0)
+
+
+# ------------------------------------------------------------------ resident tables, fixed bases
+
+@pytest.mark.parametrize("bits,window", [(1024, 4), (2048, 5), (3072, 5), (4096, 6)])
+def test_fixed_base_requests(mp, bits, window):
+    pool = 37
+    b = si.make_batch(0, "serving", pool, bits, ebits=1, sub=bits)
+    ctx = mp.MontCtx(dev(mp, b.N, IL), pool, bits, IL)
+    tables = torch.empty(mp.modexp_table_bytes(ctx, window) // 4, dtype=torch.int32, device="cuda")
+    mp.modexp_table_build(tables, dev(mp, b.a, IL), ctx, window)
+    r = si.stream(0, "serving", "other", bits)
+    nreq = 101
+    index = r.integers(0, pool, nreq).astype(np.uint32)
+    index[:3] = [0, pool - 1, 5]
+    ebits = bits
+    e = si.random_bits(si.stream(0, "serving", "exponent", bits), nreq, ebits)
+    e[0] = 0
+    Y = out_tensor(mp, nreq, b.n, IL)
+    idx_t = mp.to_device(index)
+    mp.modexp_fixed_base(Y, idx_t, dev(mp, e, IL), ebits, nreq, ctx, tables, window)
+    got = host(mp, Y, nreq, b.n, IL)
+    want = oracle.modexp(b.a[index], e, ebits, b.N[index])
+    assert_equal(got, want, f"fixed base {bits}")
+    # the same requests inside a mixed launch, next to an ordinary job
+    b2 = si.make_batch(0, "serving", 19, 1024, sub=bits + 1)
+    ctx2 = mp.MontCtx(dev(mp, b2.N, IL), 19, 1024, IL)
+    Y2 = out_tensor(mp, 19, b2.n, IL)
+    Y3 = out_tensor(mp, nreq, b.n, IL)
+    jobs = [(Y3, None, dev(mp, e, IL), ebits, ctx, window, idx_t, tables, nreq),
+            (Y2, dev(mp, b2.a, IL), dev(mp, b2.e, IL), 1024, ctx2, 4)]
+    mp.modexp_consttime_mixed(jobs, 0, mp.mixed_workspace(jobs))
+    assert_equal(host(mp, Y3, nreq, b.n, IL), want, "fixed base in a mixed launch")
+    assert_equal(host(mp, Y2, 19, b2.n, IL), oracle.modexp(b2.a, b2.e, 1024, b2.N), "ordinary job beside it")

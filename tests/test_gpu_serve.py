@@ -1,0 +1,43 @@
+"""Serving loop on the GPU: every request served in a mixed, continuously batched launch
+gives the same result as when it is computed alone and as the one-size-per-launch path;
+sampled requests match the oracle. Tolerance 0 (exact integers)."""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_served_results_equal_alone_and_plain():
+    import paper_2410_18129_gb300 as mp
+    from paper_2410_18129_gb300 import serve as sv
+    pool = sv.Pool(mp, seed=0, count=96, windows={1024: 4, 2048: 5, 3072: 5, 4096: 6})
+    tr = si.poisson_trace(0, 2e4, 360, pool.sizes)
+    cont = sv.ContinuousExecutor(pool, tr, slots=3, keep_results=True)
+    res = sv.serve(tr, cont, slots=3, max_batch=48,
+                   admission=sv.AdmissionController(free_fn=lambda: torch.cuda.mem_get_info()[0]))
+    assert len(res.results) == 360 and res.batches > 3
+    plain = sv.PlainExecutor(pool, tr, keep_results=True)
+    res_p = sv.serve(tr, plain, slots=1, max_batch=48)
+    for r in range(360):
+        assert np.array_equal(res.results[r], res_p.results[r]), r
+    # alone: one request per launch
+    IL = mp.LAYOUT_INTERLEAVED
+    sizes = pool.sizes[tr.entry]
+    sample = [r for r in range(360) if sizes[r] <= 2048][:12] + [r for r in range(360) if sizes[r] > 2048][:4]
+    for r in sample:
+        bits = int(sizes[r])
+        c = pool.classes[bits]
+        y = torch.zeros(mp.array_words(IL, 1, c["n"]), dtype=torch.int32, device="cuda")
+        idx = mp.to_device(np.array([pool.local[tr.entry[r]]], np.uint32))
+        mp.modexp_fixed_base(y, idx, mp.to_device(mp.interleave(tr.exponents[r][None, :])), bits, 1, c["ctx"],
+                             c["tables"], c["window"])
+        alone = mp.deinterleave(mp.to_host(y), 1, c["n"])[0]
+        assert np.array_equal(alone, res.results[r]), r
+    want = sv.expected(pool, tr, sample, oracle)
+    for r in sample:
+        assert np.array_equal(want[r], res.results[r]), r
+    pool.free()

@@ -1,0 +1,127 @@
+"""Serving loop host logic on CPU: admission by memory budget, continuous batching, slot
+limits and latency accounting, with a fake executor and a fake clock (no GPU)."""
+import importlib.util
+import os
+import sys
+
+import numpy as np
+
+import seeded_inputs as si
+
+# serve.py's host logic needs only numpy; load it by path so that this CPU test does not
+# need the built CUDA library (the package refuses to import without it)
+_spec = importlib.util.spec_from_file_location(
+    "mpgpu_serve", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "paper_2410_18129_gb300", "serve.py"))
+_serve = importlib.util.module_from_spec(_spec)
+sys.modules["mpgpu_serve"] = _serve          # dataclasses look their module up here
+_spec.loader.exec_module(_serve)
+AdmissionController, Handle, serve = _serve.AdmissionController, _serve.Handle, _serve.serve
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def advance(self, dt=1e-4):
+        self.t += dt
+
+
+class FakeExecutor:
+    """Each batch takes `base + per_req * size` seconds of fake time; records what it saw."""
+
+    def __init__(self, clock, base=0.01, per_req=1e-5, req_bytes=100, budget_check=None):
+        self.clock, self.base, self.per_req, self.req_bytes = clock, base, per_req, req_bytes
+        self.inflight = 0
+        self.max_inflight = 0
+        self.bytes_now = 0
+        self.max_bytes = 0
+        self.batches = []
+        self.results = {}
+
+    def bytes_for(self, reqs):
+        return int(reqs.size * self.req_bytes)
+
+    def submit(self, reqs, nbytes):
+        self.inflight += 1
+        self.max_inflight = max(self.max_inflight, self.inflight)
+        self.bytes_now += nbytes
+        self.max_bytes = max(self.max_bytes, self.bytes_now)
+        self.batches.append((self.clock(), reqs.copy()))
+        return Handle(reqs, nbytes, {"end": self.clock() + self.base + self.per_req * reqs.size})
+
+    def done(self, h):
+        return self.clock() >= h.token["end"]
+
+    def finish(self, h):
+        self.inflight -= 1
+        self.bytes_now -= h.nbytes
+
+
+def trace(rate, count, seed=0):
+    sizes = np.full(16, 1024)
+    return si.poisson_trace(seed, rate, count, sizes)
+
+
+def test_admission_budget_from_free_memory():
+    a = AdmissionController(free_fn=lambda: 10_000, fraction=0.5, reserve=1000)
+    assert a.budget == 4000
+    assert a.admit(3000) and not a.admit(1500) and a.refused == 1
+    a.release(3000)
+    assert a.admit(4000)
+    b = AdmissionController(free_fn=lambda: 10 ** 12, fraction=0.5, reserve=0, limit=777)
+    assert b.budget == 777
+
+
+def test_every_request_completes_with_consistent_latency():
+    clk = FakeClock()
+    ex = FakeExecutor(clk)
+    tr = trace(2e4, 3000)
+    res = serve(tr, ex, slots=3, max_batch=256, clock=clk, idle=clk.advance)
+    assert np.isfinite(res.latency).all() and (res.latency > 0).all()
+    assert np.allclose(res.done_at - tr.arrival, res.latency)
+    served = np.sort(np.concatenate([b for _, b in ex.batches]))
+    assert (served == np.arange(3000)).all()                 # each request exactly once
+    assert ex.max_inflight <= 3
+    assert max(b.size for _, b in ex.batches) <= 256
+
+
+def test_continuous_batching_admits_arrivals_while_busy():
+    """Requests that arrive while batches run are taken as soon as a slot frees, in arrival
+    order; with one slot the next batch starts right when the previous one ends."""
+    clk = FakeClock()
+    ex = FakeExecutor(clk, base=0.05, per_req=0.0)
+    tr = trace(1e4, 2000)
+    serve(tr, ex, slots=1, max_batch=10 ** 6, clock=clk, idle=clk.advance)
+    starts = [t for t, _ in ex.batches]
+    sizes = [b.size for _, b in ex.batches]
+    assert sizes[0] < sizes[1]                 # the first batch is small, later ones carry the queue
+    assert all(abs((s2 - s1) - 0.05) < 2e-3 for s1, s2 in zip(starts[1:-1], starts[2:]))
+    order = np.concatenate([b for _, b in ex.batches])
+    assert (order == np.arange(2000)).all()    # FIFO
+
+
+def test_admission_limits_bytes_in_flight():
+    clk = FakeClock()
+    ex = FakeExecutor(clk, req_bytes=1000)
+    adm = AdmissionController(limit=50_000, reserve=0, fraction=1.0)
+    tr = trace(1e5, 4000)
+    res = serve(tr, ex, slots=8, max_batch=1000, admission=adm, clock=clk, idle=clk.advance)
+    assert ex.max_bytes <= 50_000
+    assert res.refused > 0 and adm.in_use == 0
+
+
+def test_poisson_trace_statistics():
+    sizes = si.pool_sizes(0, 4096)
+    assert {b: int((sizes == b).sum()) for b in (1024, 2048, 3072, 4096)} == \
+        {1024: 1024, 2048: 1639, 3072: 819, 4096: 614}
+    tr = si.poisson_trace(0, 5e4, 20000, sizes)
+    gaps = np.diff(tr.arrival)
+    assert abs(gaps.mean() * 5e4 - 1) < 0.03
+    assert (gaps >= 0).all()
+    counts = np.bincount(tr.entry, minlength=4096)
+    assert counts.max() < 20 and (tr.entry < 4096).all()
+    assert all(e.shape[0] == (int(sizes[k]) + 31) // 32 for e, k in zip(tr.exponents[:50], tr.entry[:50]))
