@@ -244,8 +244,9 @@ int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *
  * block product (mad.lo.cc/madc.hi.cc chains, counts its 128 multiply-adds);
  * 3: add.cc/addc.cc chains; 4: independent mad.wide.u32 (counted as 2); 5: 8x8 block
  * product from mad.wide.u32 and 64-bit carry adds; 6: two independent 8x8 chain
- * products per iteration; 7: mode 2 on 256 threads per SM. Synchronous; allocates a
- * small scratch buffer.
+ * products per iteration; 7: mode 2 on 256 threads per SM; 8: 10x10 block of 26-bit
+ * digits summed into 64-bit columns by mad.wide.u32 (counted as 2 per product).
+ * Synchronous; allocates a small scratch buffer.
  */
 int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream);
 

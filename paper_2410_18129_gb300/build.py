@@ -55,7 +55,7 @@ def _compile(src: str, verbose: bool, extra: list[str]) -> str:
 
 def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
     os.makedirs(OUT, exist_ok=True)
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("MPG_EXTRA_FLAGS", "").split()
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:

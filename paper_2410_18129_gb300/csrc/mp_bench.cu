@@ -17,6 +17,7 @@ using namespace mpg;
 // mode 5: 8x8 block product from mad.wide.u32 plus 64-bit carry adds
 // mode 6: two independent 8x8 carry-chain block products per iteration
 // mode 7: mode 2 with 256 active threads per SM
+// mode 8: 10x10 block of 26-bit digits summed into 64-bit columns with mad.wide.u32 (counted as 2 per product)
 __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
     uint32_t a[8], b[8];
 #pragma unroll
@@ -125,8 +126,37 @@ __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+
+// mode 8 (own kernel: its 38 accumulator registers do not fit 1024 threads per SM)
+__global__ void __launch_bounds__(512) k_bench_wide(int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
+    uint32_t x[10], y[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) { x[i] = (seed * (threadIdx.x + 3 * i + 1)) & 0x3ffffffu; y[i] = (seed ^ (i * 0x9e3779b9u + threadIdx.x)) & 0x3ffffffu; }
+    uint64_t col[19];
+#pragma unroll
+    for (int c = 0; c < 19; ++c) col[c] = 0;
+    __syncthreads();
+    long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i)
+#pragma unroll
+            for (int j = 0; j < 10; ++j)
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(col[i + j]) : "r"(x[i]), "r"(y[j]));
+#pragma unroll
+        for (int i = 0; i < 10; ++i) x[i] ^= (uint32_t)col[i] & 0x3ffffffu;
+    }
+    __syncthreads();
+    long long t1 = clock64();
+    uint32_t acc = 0;
+#pragma unroll
+    for (int c = 0; c < 19; ++c) acc ^= (uint32_t)col[c] ^ (uint32_t)(col[c] >> 32);
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream) {
-    if (mode < 0 || mode > 7 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
+    if (mode < 0 || mode > 8 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MP_ERR_CUDA;
@@ -139,9 +169,15 @@ extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    k_bench<<<sms, threads, 0, st>>>(mode, 1, 12345u, sink, cyc);   // warm-up
-    cudaEventRecord(e0, st);
-    k_bench<<<sms, threads, 0, st>>>(mode, iters, 12345u, sink, cyc);
+    if (mode == 8) {
+        k_bench_wide<<<sms, 512, 0, st>>>(1, 12345u, sink, cyc);   // warm-up
+        cudaEventRecord(e0, st);
+        k_bench_wide<<<sms, 512, 0, st>>>(iters, 12345u, sink, cyc);
+    } else {
+        k_bench<<<sms, threads, 0, st>>>(mode, 1, 12345u, sink, cyc);   // warm-up
+        cudaEventRecord(e0, st);
+        k_bench<<<sms, threads, 0, st>>>(mode, iters, 12345u, sink, cyc);
+    }
     cudaEventRecord(e1, st);
     int rc = (cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) ? MP_OK : MP_ERR_CUDA;
     if (rc == MP_OK) {
@@ -151,8 +187,8 @@ extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double
         const double med = (double)c[sms / 2];
         // multiply-adds per thread: every mode is sized to 128 per iteration (mode 6: 256),
         // mode 7 runs on a quarter of the threads
-        const double per_thread = (mode == 6 ? 256.0 : 128.0) * iters;
-        const double active = mode == 7 ? 256.0 : (double)threads;
+        const double per_thread = (mode == 6 ? 256.0 : mode == 8 ? 200.0 : 128.0) * iters;
+        const double active = mode == 7 ? 256.0 : mode == 8 ? 512.0 : (double)threads;
         *per_clk_per_sm = per_thread * active / med;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);

@@ -23,6 +23,10 @@
 #pragma once
 #include "mp_limb.cuh"
 
+#ifndef MPG_PHASE_SYNC
+#define MPG_PHASE_SYNC 1
+#endif
+
 namespace mpg {
 
 template <int G_, int M_>
@@ -587,8 +591,17 @@ __device__ __noinline__ void step_reduce(Grp<S> g) {
 // Y is overwritten (it holds q afterwards).
 template <class S, int RED>
 MPG_DI void mont_mul(const Grp<S> &g, bool square) {
+#if MPG_PHASE_SYNC
+    // Every warp of the block runs the same sequence of products; a block barrier before
+    // each step keeps the warps of a scheduler inside the same step, so the instructions
+    // they fetch are shared instead of spread over the whole loop.
+    __syncthreads();
+#endif
     if (square) step_sqr<S>(g);
     else step_mul<S>(g);
+#if MPG_PHASE_SYNC
+    __syncthreads();
+#endif
     step_reduce<S, RED>(g);
 }
 
