@@ -26,6 +26,15 @@
 #ifndef MPG_PHASE_SYNC
 #define MPG_PHASE_SYNC 1
 #endif
+#ifndef MPG_ROLL
+#define MPG_ROLL 1
+#endif
+#if MPG_ROLL
+// loops over block products stay loops: one copy of the block product per phase
+#define MPG_BLOCK_LOOP _Pragma("unroll 1")
+#else
+#define MPG_BLOCK_LOOP
+#endif
 
 namespace mpg {
 
@@ -295,6 +304,7 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
     constexpr int G = S::G, M = S::M, A = S::A1;
     uint32_t V[A];
     zero<A>(V);
+    MPG_BLOCK_LOOP
     for (int j = 0; j < G; ++j) {
         const int v = (g.t - j) & (G - 1);
         mac_block<M>(V, X + j * M, Y + v * M);
@@ -342,6 +352,7 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     uint32_t V[A];
     zero<A>(V);
     bool a_done = false;
+    MPG_BLOCK_LOOP
     for (int j = 0; j < K; ++j) {
         if (j == nA) {
             flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
@@ -374,6 +385,7 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
     constexpr int G = S::G, H = S::H, A = S::A2;
     uint32_t V[A];
     zero<A>(V);
+    MPG_BLOCK_LOOP
     for (int j = 0; j <= 2 * G; ++j) {
         int u, v;
         if (j <= g.t) { u = j; v = g.t - j; }
@@ -471,6 +483,7 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
     uint32_t V[A];
     zero<A>(V);
     const int nA = 2 * G - 1 - g.t;
+    MPG_BLOCK_LOOP
     for (int j = 0; j < 2 * G - 1; ++j) {
         int u, v;
         if (j < nA) { u = g.t + 1 + j; v = 2 * G + g.t - u; }
@@ -506,6 +519,7 @@ MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *N
     uint32_t V[A];
     zero<A>(V);
     const AddendXform<M> addT{T};
+    MPG_BLOCK_LOOP
     for (int j = 0; j < G; ++j) {
         const int v = (g.t - j) & (G - 1);
         mac_block<M>(V, Qs + j * M, Ns + v * M);
@@ -548,18 +562,26 @@ MPG_DI void cond_sub(const Grp<S> &g, const uint32_t *C, uint32_t carry, const u
     gsync();
 }
 
-// Out-of-line steps of a Montgomery product. The exponentiation calls a product
-// from several places; one shared copy of each step keeps the instruction
-// footprint inside the instruction caches.
+// Steps of a Montgomery product. The kernels call the product from exactly one
+// place (a loop over the products of the job), so each step exists once in the
+// instruction stream either way; MPG_STEP_CALL keeps them as out-of-line calls.
+#ifndef MPG_STEP_CALL
+#define MPG_STEP_CALL 0
+#endif
+#if MPG_STEP_CALL
+#define MPG_STEP __device__ __noinline__
+#else
+#define MPG_STEP MPG_DI
+#endif
 template <class S>
-__device__ __noinline__ void step_mul(Grp<S> g) { phase_mul<S>(g, g.X(), g.Y(), g.T()); }
+MPG_STEP void step_mul(Grp<S> g) { phase_mul<S>(g, g.X(), g.Y(), g.T()); }
 
 template <class S>
-__device__ __noinline__ void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // squares in X, Y
+MPG_STEP void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // squares in X, Y
 
 // T (2*NP words) -> X = T * R^-1 mod N (q goes to Y). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5).
 template <class S, int RED>
-__device__ __noinline__ void step_reduce(Grp<S> g) {
+MPG_STEP void step_reduce(Grp<S> g) {
     constexpr int M = S::M, NP = S::NP;
     uint32_t *T = g.T();
     // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0]

@@ -160,11 +160,14 @@ __global__ void __launch_bounds__(TPB) k_mont(KArgs A) {
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
     gsync();
-    mont_mul<S, RED>(g, A.square != 0);
-    if (A.correct) {   // internal radix W^NP differs from the API radix W^n: multiply by W^(2NP-n) mod N
-        load_ctx<S>(g, g.Y(), A.K, A, k, valid);
-        gsync();
-        mont_mul<S, RED>(g, false);
+    // one call site; a second product when the internal radix W^NP differs from the
+    // API radix W^n: multiply by W^(2NP-n) mod N
+    for (int r = 0; r <= (A.correct ? 1 : 0); ++r) {
+        if (r) {
+            load_ctx<S>(g, g.Y(), A.K, A, k, valid);
+            gsync();
+        }
+        mont_mul<S, RED>(g, r == 0 && A.square != 0);
     }
     uint32_t x[S::M];
     lds<S::M>(x, g.X() + g.t * S::M);
@@ -244,52 +247,68 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     init_zero_block<S>(g);
     load_ctx<S>(g, g.N(), A.N, A, kc, valid);
     load_ctx<S>(g, g.NI(), A.NI, A, kc, valid);
+    // The products of the job, in order, run from ONE call site (one copy of the
+    // Montgomery product in the instruction stream):
+    //   build (modes 0, 1): G[1] = a * R^2, then G[e] = G[e-1] * G[1] for e = 2..E-1
+    //   windows (modes 0, 2): per window w squarings, then the product with the scanned entry
+    //   last: the product with 1 (leaves the Montgomery domain)
+    // Which product comes next depends only on public sizes.
+    const int nbuild = A.mode != 2 ? E - 1 : 0;
+    const int windows = (A.ebits + w - 1) / w;
+    const int nwin = A.mode != 1 ? windows * (w + 1) + 1 : 0;
     if (A.mode != 2) {
         load_api<S>(g, g.X(), A.a, A, kc, valid);
         load_ctx<S>(g, g.Y(), A.R2, A, kc, valid);
-        gsync();
-        mont_mul<S, RED>(g, false);                 // X = a*R mod N = G[1]
-        put(1, g.X());
-        load_ctx<S>(g, g.Y(), A.R1, A, kc, valid);    // G[0] = R mod N
-        put(0, g.Y());
-        for (int e = 2; e < E; ++e) {                 // G[e] = G[e-1] * G[1]
-            uint32_t x[M];
-            fetch(1, x);                              // (the product leaves q in Y)
-            sts<M>(g.Y() + g.t * M, x);
-            gsync();
-            mont_mul<S, RED>(g, false);
-            put(e, g.X());
-        }
-        if (A.mode == 1) return;
+    } else {
+        load_ctx<S>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form
     }
-    load_ctx<S>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form
     gsync();
-    const int windows = (A.ebits + w - 1) / w;
-    for (int win = windows - 1; win >= 0; --win) {
-        for (int s = 0; s < w; ++s) mont_mul<S, RED>(g, true);
-        const uint32_t bsel = window_bits(A, k, valid, win * w, w);
-        // masked scan of the whole table: every entry is read, one is kept
-        uint32_t acc[M];
-        zero<M>(acc);
-        for (int e = 0; e < E; ++e) {
-            const uint32_t m = mask_if_equal((uint32_t)e, bsel);
-            uint32_t x[M];
-            fetch(e, x);
+    for (int op = 0; op < nbuild + nwin; ++op) {
+        bool square = false;
+        if (op >= nbuild) {
+            const int r = op - nbuild;
+            const int i = r / (w + 1), s = r - i * (w + 1);
+            if (i == windows) {                         // the product with 1
+                uint32_t x[M];
+                zero<M>(x);
+                if (g.t == 0) x[0] = 1u;
+                sts<M>(g.Y() + g.t * M, x);
+                gsync();
+            } else if (s < w) {
+                square = true;
+            } else {   // masked scan of the whole table: every entry is read, one is kept
+                const uint32_t bsel = window_bits(A, k, valid, (windows - 1 - i) * w, w);
+                uint32_t acc[M];
+                zero<M>(acc);
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t m = mask_if_equal((uint32_t)e, bsel);
+                    uint32_t x[M];
+                    fetch(e, x);
 #pragma unroll
-            for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
+                    for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
+                }
+                sts<M>(g.Y() + g.t * M, acc);
+                gsync();
+            }
         }
-        sts<M>(g.Y() + g.t * M, acc);
-        gsync();
-        mont_mul<S, RED>(g, false);
+        mont_mul<S, RED>(g, square);
+        if (op < nbuild) {
+            put(op + 1, g.X());
+            if (op == 0) {                              // G[0] = R mod N
+                load_ctx<S>(g, g.Y(), A.R1, A, kc, valid);
+                put(0, g.Y());
+            }
+            if (op + 1 < nbuild) {                      // next: G[op+2] = G[op+1] * G[1]
+                uint32_t x[M];                          // (the product leaves q in Y)
+                fetch(1, x);
+                sts<M>(g.Y() + g.t * M, x);
+            } else if (A.mode == 0) {
+                load_ctx<S>(g, g.X(), A.R1, A, kc, valid);   // Y_acc = 1 in Montgomery form
+            }
+            gsync();
+        }
     }
-    {   // leave the Montgomery domain: X * 1 * R^-1
-        uint32_t x[M];
-        zero<M>(x);
-        if (g.t == 0) x[0] = 1u;
-        sts<M>(g.Y() + g.t * M, x);
-        gsync();
-        mont_mul<S, RED>(g, false);
-    }
+    if (A.mode == 1) return;
     uint32_t x[M];
     lds<M>(x, g.X() + g.t * M);
     gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
