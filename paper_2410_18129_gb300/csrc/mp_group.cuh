@@ -23,18 +23,8 @@
 #pragma once
 #include "mp_limb.cuh"
 
-#ifndef MPG_PHASE_SYNC
-#define MPG_PHASE_SYNC 1
-#endif
-#ifndef MPG_ROLL
-#define MPG_ROLL 1
-#endif
-#if MPG_ROLL
 // loops over block products stay loops: one copy of the block product per phase
 #define MPG_BLOCK_LOOP _Pragma("unroll 1")
-#else
-#define MPG_BLOCK_LOOP
-#endif
 
 namespace mpg {
 
@@ -564,24 +554,16 @@ MPG_DI void cond_sub(const Grp<S> &g, const uint32_t *C, uint32_t carry, const u
 
 // Steps of a Montgomery product. The kernels call the product from exactly one
 // place (a loop over the products of the job), so each step exists once in the
-// instruction stream either way; MPG_STEP_CALL keeps them as out-of-line calls.
-#ifndef MPG_STEP_CALL
-#define MPG_STEP_CALL 0
-#endif
-#if MPG_STEP_CALL
-#define MPG_STEP __device__ __noinline__
-#else
-#define MPG_STEP MPG_DI
-#endif
+// instruction stream although it is inlined.
 template <class S>
-MPG_STEP void step_mul(Grp<S> g) { phase_mul<S>(g, g.X(), g.Y(), g.T()); }
+MPG_DI void step_mul(Grp<S> g) { phase_mul<S>(g, g.X(), g.Y(), g.T()); }
 
 template <class S>
-MPG_STEP void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // squares in X, Y
+MPG_DI void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // squares in X, Y
 
 // T (2*NP words) -> X = T * R^-1 mod N (q goes to Y). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5).
 template <class S, int RED>
-MPG_STEP void step_reduce(Grp<S> g) {
+MPG_DI void step_reduce(Grp<S> g) {
     constexpr int M = S::M, NP = S::NP;
     uint32_t *T = g.T();
     // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0]
@@ -613,17 +595,8 @@ MPG_STEP void step_reduce(Grp<S> g) {
 // Y is overwritten (it holds q afterwards).
 template <class S, int RED>
 MPG_DI void mont_mul(const Grp<S> &g, bool square) {
-#if MPG_PHASE_SYNC
-    // Every warp of the block runs the same sequence of products; a block barrier before
-    // each step keeps the warps of a scheduler inside the same step, so the instructions
-    // they fetch are shared instead of spread over the whole loop.
-    __syncthreads();
-#endif
     if (square) step_sqr<S>(g);
     else step_mul<S>(g);
-#if MPG_PHASE_SYNC
-    __syncthreads();
-#endif
     step_reduce<S, RED>(g);
 }
 
