@@ -166,6 +166,42 @@ MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
     zero<2 * B + 2>(V);
 }
 
+// store a slot's running sum without clearing it (low B words to out_lo, the rest to
+// spill). A thread accumulates its two slots in ONE register sum: it parks the sum when
+// the first slot is complete and recovers the second slot at the end as the final sum
+// minus the parked one (unpark_sub), so the loop body never clears registers.
+template <int B>
+MPG_DI void park(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
+#if MPG_PARK_SCALAR
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(out_lo), b = (uint32_t)__cvta_generic_to_shared(spill);
+#pragma unroll
+    for (int j = 0; j < B; ++j) asm volatile("st.shared.u32 [%0], %1;" ::"r"(a + 4 * j), "r"(V[j]) : "memory");
+#pragma unroll
+    for (int j = 0; j < B + 2; ++j) asm volatile("st.shared.u32 [%0], %1;" ::"r"(b + 4 * j), "r"(V[B + j]) : "memory");
+    return;
+#endif
+    uint32_t lo[B], hi[B + 2];
+#pragma unroll
+    for (int j = 0; j < B; ++j) lo[j] = V[j];
+#pragma unroll
+    for (int j = 0; j < B + 2; ++j) hi[j] = V[B + j];
+    sts<B>(out_lo, lo);
+    sts<B + 2>(spill, hi);
+}
+
+// V -= the sum parked at out_lo / spill (exact: V holds the parked sum plus more)
+template <int B>
+MPG_DI void unpark_sub(uint32_t (&V)[2 * B + 2], const uint32_t *out_lo, const uint32_t *spill) {
+    uint32_t lo[B], hi[B + 2];
+    lds<B>(lo, out_lo);
+    lds<B + 2>(hi, spill);
+    sub_cc(V[0], lo[0]);
+#pragma unroll
+    for (int j = 1; j < B; ++j) subc_cc(V[j], lo[j]);
+#pragma unroll
+    for (int j = 0; j < B + 2; ++j) subc_cc(V[B + j], hi[j]);
+}
+
 // overflow words of the predecessor slot, passed between lanes with shuffles
 template <int G, int PAT>
 MPG_DI void pred_overflow(int t, int gbase, const uint32_t (&ovA)[2], const uint32_t (&ovB)[2],
@@ -298,9 +334,10 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
     for (int j = 0; j < G; ++j) {
         const int v = (g.t - j) & (G - 1);
         mac_block<M>(V, X + j * M, Y + v * M);
-        if (j == g.t) flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+        if (j == g.t) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
     }
-    flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
+    unpark_sub<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+    park<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
     gsync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
@@ -341,21 +378,18 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     constexpr int K = G / 2;                    // max of nA + nB over the group
     uint32_t V[A];
     zero<A>(V);
-    bool a_done = false;
     MPG_BLOCK_LOOP
     for (int j = 0; j < K; ++j) {
-        if (j == nA) {
-            flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
-            a_done = true;
-        }
+        if (j == nA) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
         int u, v;
         if (j < nA) { u = j; v = g.t - j; }
         else { u = g.t + 1 + (j - nA); v = G + g.t - u; }
         const bool live = j < nA + nB;
         mac_block<M>(V, X + (live ? u : 0) * M, live ? X + v * M : g.Z());
     }
-    if (!a_done) flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
-    flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
+    if (nA == K) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+    unpark_sub<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+    park<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
     uint32_t x[M], P[2 * M];
     lds<M>(x, X + g.t * M);
     gsync();                                    // all reads of X are done
@@ -381,9 +415,10 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
         if (j <= g.t) { u = j; v = g.t - j; }
         else { u = j - g.t - 1; v = 2 * G - j; }
         mac_block<H>(V, X + u * H, Y + v * H);
-        if (j == g.t) flush<H>(V, Q + g.t * H, g.P() + g.t * (H + 2));
+        if (j == g.t) park<H>(V, Q + g.t * H, g.P() + g.t * (H + 2));
     }
-    flush<H>(V, Q + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
+    unpark_sub<H>(V, Q + g.t * H, g.P() + g.t * (H + 2));
+    park<H>(V, Q + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
     gsync();
     uint32_t in0[H + 2];
     zero<H + 2>(in0);
@@ -479,9 +514,10 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
         if (j < nA) { u = g.t + 1 + j; v = 2 * G + g.t - u; }
         else { u = j + 1; v = 4 * G - 2 - g.t - j; }
         mac_block<H>(V, Qs + u * H, Ns + v * H);
-        if (j == nA - 1) flush<H>(V, C + g.t * H, g.P() + g.t * (H + 2));
+        if (j == nA - 1) park<H>(V, C + g.t * H, g.P() + g.t * (H + 2));
     }
-    flush<H>(V, C + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
+    unpark_sub<H>(V, C + g.t * H, g.P() + g.t * (H + 2));
+    park<H>(V, C + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
     // sum Z over the group (butterfly; every lane gets the total)
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
