@@ -172,14 +172,6 @@ MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
 // minus the parked one (unpark_sub), so the loop body never clears registers.
 template <int B>
 MPG_DI void park(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
-#if MPG_PARK_SCALAR
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(out_lo), b = (uint32_t)__cvta_generic_to_shared(spill);
-#pragma unroll
-    for (int j = 0; j < B; ++j) asm volatile("st.shared.u32 [%0], %1;" ::"r"(a + 4 * j), "r"(V[j]) : "memory");
-#pragma unroll
-    for (int j = 0; j < B + 2; ++j) asm volatile("st.shared.u32 [%0], %1;" ::"r"(b + 4 * j), "r"(V[B + j]) : "memory");
-    return;
-#endif
     uint32_t lo[B], hi[B + 2];
 #pragma unroll
     for (int j = 0; j < B; ++j) lo[j] = V[j];
