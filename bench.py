@@ -122,6 +122,35 @@ def cpu_oracle_rate(b, ebits, budget_s: float, threads: int = 0):
     return count / dt, cores, count, dt
 
 
+def sources_digest() -> str:
+    """Digest of the CUDA sources and the C header: a recorded ncu figure applies only to the
+    kernel built from exactly these sources."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2410_18129_gb300", "csrc", "*.cu*")) +
+                   glob.glob(os.path.join(ROOT, "paper_2410_18129_gb300", "csrc", "*.h")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, instances: int):
+    """DRAM bytes (read + write) per launch from profiles/traffic.json, scaled to `instances`;
+    None when there is no record or the kernel sources changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_digest") != sources_digest():
+        return None
+    return rec["dram_bytes_per_launch"] * instances / rec["instances"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -289,6 +318,7 @@ def main():
         want = oracle.modexp(b.a[idx], b.e[idx], ebits, b.N[idx])
         parity = {"sampled": int(idx.size), "mismatches": int((got != want).any(axis=1).sum())}
 
+    traffic = recorded_traffic("k_modexp_2048_w5", B)
     imad = modexp_imad(BITS, ebits, WINDOW, "trunc")
     achieved = imad * B / (ms_step / 1e3) / 1e12
     peak_clock = 2070.0
@@ -300,7 +330,8 @@ def main():
     peak = sms * imad_rate * peak_clock * 1e6 / 1e12
     obs_clock = clocks["sm_mhz"] or imad_mhz
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu, same kernel sources)",
                 "peak_basis": f"{sms} SMs x {imad_rate:.1f} IMAD/clk/SM (measured) x {peak_clock:.0f} MHz max clock",
                 "frac_at_observed_clock": achieved / (sms * imad_rate * obs_clock * 1e6 / 1e12),
                 "imad_per_modexp": imad}

@@ -385,7 +385,7 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     uint32_t x[M], P[2 * M];
     lds<M>(x, X + g.t * M);
     gsync();                                    // all reads of X are done
-    block_mul<M>(P, x, x);
+    block_sqr<M>(P, x);
     sts<2 * M>(D + 2 * g.t * M, P);
     gsync();
     uint32_t in0[M + 2];

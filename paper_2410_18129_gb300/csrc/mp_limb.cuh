@@ -74,6 +74,43 @@ MPG_DI void block_mul(uint32_t (&P)[2 * B], const uint32_t (&x)[B], const uint32
     }
 }
 
+// P = x^2 (2B words) from the B(B-1)/2 cross products x_i x_j (i < j), doubled, plus the B
+// squares x_i^2 at column 2i (Alg. 2's split, on one block).
+template <int B>
+MPG_DI void block_sqr(uint32_t (&P)[2 * B], const uint32_t (&x)[B]) {
+#pragma unroll
+    for (int j = 0; j < 2 * B; ++j) P[j] = 0;
+#pragma unroll
+    for (int i = 0; i + 1 < B; ++i) {
+        // two chains per row (j - i odd, j - i even): their (lo, hi) pairs never share a column
+#pragma unroll
+        for (int par = 1; par <= 2; ++par) {
+            if (i + par < B) {
+#pragma unroll
+                for (int j = i + par; j < B; j += 2) {
+                    if (j == i + par) mad_lo_cc(P[i + j], x[i], x[j]);
+                    else madc_lo_cc(P[i + j], x[i], x[j]);
+                    madc_hi_cc(P[i + j + 1], x[i], x[j]);
+                }
+                const int jl = i + par + 2 * ((B - 1 - (i + par)) / 2);   // last j of the chain
+#pragma unroll
+                for (int p = i + jl + 2; p <= i + B; ++p) addc_cc(P[p], 0u);
+            }
+        }
+    }
+    // double: the cross sum is below W^(2B) / 2
+#pragma unroll
+    for (int k = 2 * B - 1; k > 0; --k) P[k] = __funnelshift_l(P[k - 1], P[k], 1);
+    P[0] <<= 1;
+    mad_lo_cc(P[0], x[0], x[0]);
+    madc_hi_cc(P[1], x[0], x[0]);
+#pragma unroll
+    for (int i = 1; i < B; ++i) {
+        madc_lo_cc(P[2 * i], x[i], x[i]);
+        madc_hi_cc(P[2 * i + 1], x[i], x[i]);
+    }
+}
+
 // V[0..2B+2) += P[0..2B)
 template <int B>
 MPG_DI void acc_add(uint32_t (&V)[2 * B + 2], const uint32_t (&P)[2 * B]) {
