@@ -122,6 +122,17 @@ def cpu_oracle_rate(b, ebits, budget_s: float, threads: int = 0):
     return count / dt, cores, count, dt
 
 
+def _load_replicas():
+    """The replica helpers, loaded by path (they need no CUDA library)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "mpgpu_replicas", os.path.join(ROOT, "paper_2410_18129_gb300", "replicas.py"))
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules["mpgpu_replicas"] = mod
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def sources_digest() -> str:
     """Digest of the CUDA sources and the C header: a recorded ncu figure applies only to the
     kernel built from exactly these sources."""
@@ -172,16 +183,16 @@ def main():
     if args.workload == "serving":
         return bench_serving(args)
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    reps = _load_replicas()
+    info = reps.rank_info()
+    world, rank, local = info.world, info.rank, info.local
 
     import numpy as np
     import seeded_inputs as si
 
     procs = min(16, os.cpu_count() or 1)
     # inputs are generated before any CUDA call (the prime pool uses spawned workers)
-    b = si.batch_2048(seed=rank, batch=args.batch, procs=procs)
+    b = si.batch_2048(seed=reps.rank_seed(0, rank), batch=args.batch, procs=procs)
     ebits = b.ebits
 
     if args.impl == "reference":
@@ -211,9 +222,7 @@ def main():
     import torch
     import paper_2410_18129_gb300 as mp
 
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    reps.init(info)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     IL = mp.LAYOUT_INTERLEAVED
@@ -229,8 +238,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        reps.barrier(info)
         torch.cuda.synchronize()
 
     def step(red=mp.RED_TRUNCATED):
@@ -245,12 +253,7 @@ def main():
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reps.max_over_ranks(info, e0.elapsed_time(e1), device=dev)
 
     # roofline denominator: measured integer multiply-add rate per SM per clock
     imad_rate, imad_mhz = mp.bench_imad(0, 2000)
@@ -265,7 +268,7 @@ def main():
         ms = timed(step, args.steps)
     clocks = clk.summary()
     ms_step = ms / args.steps
-    value = world * B / (ms_step / 1e3)
+    value = reps.job_rate(info, B, ms_step)
 
     if args.quick:
         if rank == 0:
