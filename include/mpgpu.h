@@ -22,7 +22,10 @@
  *   - Montgomery radix R = 2^(32n). Montgomery-domain values are x*R mod N.
  *     Every Montgomery output is canonical (< N): the library always performs the
  *     final conditional subtraction that Alg. 5 leaves optional, because R = 2^(32n)
- *     leaves no slack above a modulus whose top bit is set.
+ *     leaves no slack above a modulus whose top bit is set. Inside an exponentiation
+ *     whose size is padded (4N <= 2^(32*NP), NP the padded word count of the size
+ *     class) the products skip it and stay below 2N (the slack of Alg. 3/Alg. 5);
+ *     the result is made canonical once at the end.
  *   - Preconditions of mont_* and modexp: inputs < N, N odd with its top bit (bits-1) set.
  *     Violations give unspecified (but memory-safe) results.
  */

@@ -357,6 +357,8 @@ static void fill_ctx_args(KArgs &A, const mont_ctx *c) {
     A.correct = (c->n != c->np) ? 1 : 0;
     A.index = nullptr;
     A.mode = 0;
+    // exponentiation only (mont_mul/mont_sqr results are always canonical): 4N <= W^NP
+    A.lazy = (c->bits + 2 <= 32u * c->np) ? 1 : 0;
 }
 
 void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }

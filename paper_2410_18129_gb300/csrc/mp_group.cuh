@@ -590,8 +590,10 @@ template <class S>
 MPG_DI void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // squares in X, Y
 
 // T (2*NP words) -> X = T * R^-1 mod N (q goes to Y). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5).
+// lazy: no final subtraction; with 4N <= R and T < 4N^2 the result stays below 2N (the slack
+// that lets the paper's Alg. 3 and Alg. 5 skip it).
 template <class S, int RED>
-MPG_DI void step_reduce(Grp<S> g) {
+MPG_DI void step_reduce(Grp<S> g, bool lazy) {
     constexpr int M = S::M, NP = S::NP;
     uint32_t *T = g.T();
     // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0]
@@ -610,22 +612,29 @@ MPG_DI void step_reduce(Grp<S> g) {
     phase_mullo<S>(g, T, g.NI(), g.Q());
     if constexpr (RED == 0) {
         const uint32_t carry = phase_mulhi<S>(g, g.Q(), g.N(), T, c_add, low_zero, g.X());
-        cond_sub<S>(g, g.X(), carry, g.N(), g.X());
+        if (!lazy) cond_sub<S>(g, g.X(), carry, g.N(), g.X());
     } else {
         (void)c_add;
         (void)low_zero;
         const uint32_t carry = phase_fma<S>(g, g.Q(), g.N(), T);
-        cond_sub<S>(g, T + NP, carry, g.N(), g.X());
+        if (!lazy) {
+            cond_sub<S>(g, T + NP, carry, g.N(), g.X());
+        } else {
+            uint32_t x[M];
+            lds<M>(x, T + NP + g.t * M);
+            sts<M>(g.X() + g.t * M, x);
+            gsync();
+        }
     }
 }
 
 // X <- X * Y * R^-1 mod N (or X^2 * R^-1 when square): X, Y, N, N' in shared memory.
 // Y is overwritten (it holds q afterwards).
 template <class S, int RED>
-MPG_DI void mont_mul(const Grp<S> &g, bool square) {
+MPG_DI void mont_mul(const Grp<S> &g, bool square, bool lazy) {
     if (square) step_sqr<S>(g);
     else step_mul<S>(g);
-    step_reduce<S, RED>(g);
+    step_reduce<S, RED>(g, lazy);
 }
 
 }  // namespace mpg

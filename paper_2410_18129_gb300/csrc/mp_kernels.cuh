@@ -89,6 +89,7 @@ struct KArgs {
     const uint32_t *index;   // fixed-base requests: request k uses context instance index[k]
     size_t cbatch;           // instances of the context arrays and tables (== batch without index)
     int mode;                // exponentiation: 0 build the table and run, 1 build only, 2 run on a resident table
+    int lazy;                // exponentiation: 4N <= W^NP, products skip the final subtraction (results < 2N)
 };
 
 template <class S>
@@ -126,10 +127,23 @@ MPG_DI void load_ctx(const Grp<S> &g, uint32_t *dst, const uint32_t *src, const 
     sts<S::M>(dst + g.t * S::M, x);
 }
 
+// Blocks per SM that the shared memory of a shape allows (228 KB per SM, 1 KB of it reserved per
+// block), but never so many that a thread gets fewer than 64 registers. The kernels declare it as
+// their minimum blocks per SM, so the compiler may use every register that this occupancy leaves
+// (large blocks of words want many).
+template <class S, int TPB>
+constexpr int blocks_per_sm() {
+    constexpr long smem = (long)(TPB / S::G) * S::WORDS * 4 + 1024;
+    constexpr long by_smem = 233472L / smem;
+    constexpr long by_regs = 65536L / (TPB * 64L);
+    constexpr long b = by_smem < by_regs ? by_smem : by_regs;
+    return b < 1 ? 1 : (int)b;
+}
+
 // ------------------------------------------------------------------ mp_mul / mp_sqr
 
 template <class S, int TPB>
-__global__ void __launch_bounds__(TPB) k_mul(KArgs A) {
+__global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mul(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(TPB) k_mul(KArgs A) {
 // ------------------------------------------------------------------ mont_mul / mont_sqr
 
 template <class S, int TPB, int RED>
-__global__ void __launch_bounds__(TPB) k_mont(KArgs A) {
+__global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mont(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
@@ -167,7 +181,7 @@ __global__ void __launch_bounds__(TPB) k_mont(KArgs A) {
             load_ctx<S>(g, g.Y(), A.K, A, k, valid);
             gsync();
         }
-        mont_mul<S, RED>(g, r == 0 && A.square != 0);
+        mont_mul<S, RED>(g, r == 0 && A.square != 0, false);
     }
     uint32_t x[S::M];
     lds<S::M>(x, g.X() + g.t * S::M);
@@ -291,7 +305,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
                 gsync();
             }
         }
-        mont_mul<S, RED>(g, square);
+        mont_mul<S, RED>(g, square, A.lazy != 0);
         if (op < nbuild) {
             put(op + 1, g.X());
             if (op == 0) {                              // G[0] = R mod N
@@ -309,13 +323,14 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
         }
     }
     if (A.mode == 1) return;
+    if (A.lazy) cond_sub<S>(g, g.X(), 0u, g.N(), g.X());   // X <= N here: canonical result
     uint32_t x[M];
     lds<M>(x, g.X() + g.t * M);
     gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
 }
 
 template <class S, int TPB, int RED>
-__global__ void __launch_bounds__(TPB) k_modexp(KArgs A) {
+__global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_modexp(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;

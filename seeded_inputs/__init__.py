@@ -26,7 +26,7 @@ import numpy as np
 
 FIELDS = {"modulus": 1, "base": 2, "exponent": 3, "prime": 4, "size": 5, "other": 6,
           "arrival": 7, "pool": 8}
-WORKLOADS = {"plain_small": 1, "batch_2048": 2, "batch_4096": 3, "mixed": 4, "serving": 5,
+WORKLOADS = {"plain_small": 1, "batch_2048": 2, "batch_4096": 3, "mixed": 4, "serving": 5, "lazy": 6,
              "test": 99}
 
 

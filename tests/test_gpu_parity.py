@@ -173,6 +173,41 @@ def test_modexp(mp, bits, batch, window, layout):
         assert_equal(host(mp, Y, batch, b.n, layout), want, f"modexp {bits} w={window} red={red}")
 
 
+@pytest.mark.parametrize("bits", [254, 255, 1022, 1023, 2046, 4108, 4606, 4607])
+def test_modexp_lazy_slack_boundary(mp, bits):
+    """Sizes on both sides of 4N <= W^NP, where the exponentiation keeps products below 2N
+    without the final subtraction (lazy reduction) and canonicalises once at the end:
+    largest moduli, bases N-1 and N-2, all-ones exponents, random ones; both reductions."""
+    n = (bits + 31) // 32
+    r = si.stream(0, "test", "other", 7000 + bits)
+    Ns = [2 ** bits - 1, 2 ** (bits - 1) + 1] + [si.to_int(v) for v in si.random_odd_moduli(r, 4, bits)]
+    rows = []
+    for N in Ns:
+        for a in (N - 1, N - 2, 3):
+            for e in (2 ** bits - 1, si.to_int(si.random_bits(r, 1, bits)[0])):
+                rows.append((N, a, e))
+    B = len(rows)
+    N = si.from_ints([x[0] for x in rows], n)
+    a = si.from_ints([x[1] for x in rows], n)
+    e = si.from_ints([x[2] for x in rows], n)
+    ctx = mp.MontCtx(dev(mp, N, IL), B, bits, IL)
+    want = [pow(x[1], x[2], x[0]) for x in rows]
+    for red in (0, 1):
+        Y = out_tensor(mp, B, n, IL)
+        mp.modexp_consttime(Y, dev(mp, a, IL), dev(mp, e, IL), bits, ctx, 5, red)
+        got = host(mp, Y, B, n, IL)
+        bad = [k for k in range(B) if si.to_int(got[k]) != want[k]]
+        assert not bad, f"{bits} bits red={red}: {len(bad)} wrong, first {bad[:4]}"
+    # resident tables + fixed-base requests use the same products
+    tables = torch.empty(mp.modexp_table_bytes(ctx, 4) // 4, dtype=torch.int32, device="cuda")
+    mp.modexp_table_build(tables, dev(mp, a, IL), ctx, 4)
+    index = np.arange(B, dtype=np.uint32)[::-1].copy()
+    Y = out_tensor(mp, B, n, IL)
+    mp.modexp_fixed_base(Y, mp.to_device(index), dev(mp, e[index], IL), bits, B, ctx, tables, 4)
+    got = host(mp, Y, B, n, IL)
+    assert all(si.to_int(got[k]) == want[index[k]] for k in range(B)), f"{bits} bits, fixed base"
+
+
 def test_modexp_window_independence_and_workspace(mp):
     bits, batch = 1024, 33
     b = si.make_batch(0, "test", batch, bits, sub=31)
