@@ -282,11 +282,14 @@ def main():
     for _ in range(1):
         step(mp.RED_FULL)
     ms_full = timed(lambda: step(mp.RED_FULL), max(2, args.steps // 2)) / max(2, args.steps // 2)
+    # word-serial CIOS (Alg. 4) for comparison
+    step(mp.RED_CIOS)
+    ms_cios = timed(lambda: step(mp.RED_CIOS), max(2, args.steps // 2)) / max(2, args.steps // 2)
 
     # Montgomery products over the same batch
     C = torch.zeros_like(A)
     mm = {}
-    for red, nm in ((mp.RED_TRUNCATED, "trunc"), (mp.RED_FULL, "full")):
+    for red, nm in ((mp.RED_TRUNCATED, "trunc"), (mp.RED_FULL, "full"), (mp.RED_CIOS, "cios")):
         for _ in range(3):
             mp.mont_mul(C, A, Bv, ctx, red)
         k = 50
@@ -362,8 +365,9 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clocks,
             "modexp_full_reduction_per_s": world * B / (ms_full / 1e3),
-            "montmul_per_s": {"trunc": mm["trunc"], "full": mm["full"]},
-            "montsqr_per_s": {"trunc": mm["trunc_sqr"], "full": mm["full_sqr"]},
+            "modexp_cios_per_s": world * B / (ms_cios / 1e3),
+            "montmul_per_s": {"trunc": mm["trunc"], "full": mm["full"], "cios": mm["cios"]},
+            "montsqr_per_s": {"trunc": mm["trunc_sqr"], "full": mm["full_sqr"], "cios": mm["cios_sqr"]},
             "parity": parity,
             "imad_microbench": {"per_clk_per_sm": imad_rate, "implied_mhz": imad_mhz},
         }

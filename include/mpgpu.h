@@ -53,7 +53,8 @@ typedef enum {
 
 typedef enum { MP_LAYOUT_INSTANCE_MAJOR = 0, MP_LAYOUT_INTERLEAVED = 1 } mp_layout;
 typedef enum { MP_ALGO_AUTO = 0, MP_ALGO_SCHOOLBOOK = 1, MP_ALGO_KARATSUBA = 2 } mp_algo;
-typedef enum { MP_RED_TRUNCATED = 0, MP_RED_FULL = 1 } mp_red;
+/* Reductions: truncated (Alg. 6), classical (Alg. 3/5), word-serial CIOS (Alg. 4). */
+typedef enum { MP_RED_TRUNCATED = 0, MP_RED_FULL = 1, MP_RED_CIOS = 2 } mp_red;
 
 /* Opaque per-batch Montgomery context: device copies of N, N', R mod N, R^2 mod N. */
 typedef struct mont_ctx mont_ctx;
@@ -118,7 +119,9 @@ int mont_ctx_export(const mont_ctx *ctx, int which, uint32_t *dst, void *stream)
  * Batch Montgomery product c_k = a_k * b_k * R^{-1} mod N_k (Alg. 3 with B_mul,
  * Alg. 5/6): red = MP_RED_TRUNCATED computes only the low half of q = T*N' mod R
  * and only the high half of q*N (Alg. 6, Thm. 1, Thm. 2); MP_RED_FULL forms the
- * whole T + q*N (Alg. 3, B_fma). Both give the same canonical result.
+ * whole T + q*N (Alg. 3, B_fma); MP_RED_CIOS interleaves the product and the
+ * reduction word by word (Alg. 4: per word a_i, Y += a_i*B, q = (Y mod W)*n0',
+ * Y = (Y + q*N)/W; needs only n0' = N' mod W). All give the same canonical result.
  * a, b, c: n words per instance in the context layout; c may alias a or b.
  */
 int mont_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, const mont_ctx *ctx, mp_red red,
@@ -159,6 +162,7 @@ int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uin
  * ONE kernel launch: blocks pull tiles of instances from an atomic counter, the
  * costliest job first, so the launch can be captured in a CUDA graph together with
  * its input copies. Results equal those of modexp_consttime on each job.
+ * red: MP_RED_TRUNCATED or MP_RED_FULL (MP_RED_CIOS: MP_ERR_UNIMPLEMENTED).
  * workspace: at least modexp_mixed_workspace_bytes(jobs, njobs) bytes, 256-byte
  * aligned (window tables plus the tile counter, which the call resets on `stream`).
  */

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmpgpu.so")
 
 LAYOUT_INSTANCE_MAJOR, LAYOUT_INTERLEAVED = 0, 1
 ALGO_AUTO, ALGO_SCHOOLBOOK, ALGO_KARATSUBA = 0, 1, 2
-RED_TRUNCATED, RED_FULL = 0, 1
+RED_TRUNCATED, RED_FULL, RED_CIOS = 0, 1, 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libmpgpu.so is not built ({LIB_PATH}); run __graft_entry__.build() "

@@ -366,7 +366,7 @@ void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }
 static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
                        mp_algo algo, bool square, void *stream) {
     if (!out || !a || (!square && !b) || !c) return MP_ERR_ARG;
-    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
     if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
     if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(out) || !aligned16(a) || (!square && !aligned16(b))))
@@ -449,7 +449,7 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
                                 const mont_ctx *c, uint32_t window, mp_red red, mp_algo algo, void *workspace,
                                 size_t workspace_bytes, void *stream) {
     if (!y || !base || !c || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
-    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
     if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
     if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
     if (window == 0) window = tuned_window(c->bits);
@@ -492,7 +492,7 @@ extern "C" size_t modexp_table_bytes(const mont_ctx *c, uint32_t window) {
 extern "C" int modexp_table_build(void *tables, size_t bytes, const uint32_t *base, const mont_ctx *c,
                                   uint32_t window, mp_red red, void *stream) {
     if (!tables || !base || !c) return MP_ERR_ARG;
-    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
     if (window == 0 || window > 6) return MP_ERR_SIZE;
     if (!aligned16(tables) || (c->layout == MP_LAYOUT_INTERLEAVED && !aligned16(base))) return MP_ERR_ALIGN;
     if (bytes < modexp_table_bytes(c, window)) return MP_ERR_NOMEM;
@@ -507,7 +507,7 @@ extern "C" int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint3
                                  size_t nreq, const mont_ctx *c, const void *tables, uint32_t window, mp_red red,
                                  void *stream) {
     if (!y || !index || !c || !tables || (exp_bits > 0 && !exp) || nreq == 0) return MP_ERR_ARG;
-    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
     if (window == 0 || window > 6) return MP_ERR_SIZE;
     if (!aligned16(tables) || (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || (exp && !aligned16(exp)))))
         return MP_ERR_ALIGN;
@@ -557,7 +557,7 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
                                         const mont_ctx *c, uint32_t window, mp_red red, mp_algo algo,
                                         void *stream) {
     if (!y || !base || !c || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
-    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
     if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
     if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
     if (window == 0) window = tuned_window(c->bits);

@@ -628,13 +628,119 @@ MPG_DI void step_reduce(Grp<S> g, bool lazy) {
     }
 }
 
+// ------------------------------------------------------------------ CIOS (Alg. 4)
+//
+// Word-serial Montgomery product (the paper's CIOS-inspired batch algorithm): for each
+// word a_i of X, Y += a_i * B, q = (Y mod W) * n0' mod W, Y = (Y + q * N) / W. Thread t
+// keeps words tM .. tM+M-1 of Y plus two carry-save words above them (positions
+// (t+1)M and (t+1)M+1, which overlap the next thread's words), so a step needs no
+// carry propagation across threads: the division by W moves every word down one place
+// and thread t+1's lowest word joins thread t's word M-1. The carry-save sum stays
+// below 3 W^(M+1) per thread. Inter-thread carries are resolved once at the end.
+// Rotation: in step s of a body, logical word j of the thread's M+2 words sits in
+// register (j + s) mod (M+2), so the shift costs no register moves; a body of M+2 steps
+// brings the rotation back to 0.
+
+// logical y[0 .. M+1] += x * v[0 .. M-1] (rotation R)
+template <int M, int R>
+MPG_DI void cios_rowmac(uint32_t (&y)[M + 2], uint32_t x, const uint32_t (&v)[M]) {
+    constexpr int L = M + 2;
+    mad_lo_cc(y[R % L], x, v[0]);
+    madc_hi_cc(y[(1 + R) % L], x, v[0]);
+#pragma unroll
+    for (int j = 2; j < M; j += 2) {
+        madc_lo_cc(y[(j + R) % L], x, v[j]);
+        madc_hi_cc(y[(j + 1 + R) % L], x, v[j]);
+    }
+    addc_cc(y[(M + R) % L], 0u);
+    addc(y[(M + 1 + R) % L], 0u);
+    mad_lo_cc(y[(1 + R) % L], x, v[1]);
+    madc_hi_cc(y[(2 + R) % L], x, v[1]);
+#pragma unroll
+    for (int j = 3; j < M; j += 2) {
+        madc_lo_cc(y[(j + R) % L], x, v[j]);
+        madc_hi_cc(y[(j + 1 + R) % L], x, v[j]);
+    }
+    addc(y[(M + 1 + R) % L], 0u);
+}
+
+// CNT steps starting at word i of X, the first with rotation R
+template <class S, int R, int CNT>
+MPG_DI void cios_steps(const Grp<S> &g, uint32_t (&y)[S::M + 2], int i, const uint32_t (&b)[S::M],
+                       const uint32_t (&nn)[S::M], uint32_t n0i) {
+    if constexpr (CNT > 0) {
+        constexpr int M = S::M, L = M + 2, G = S::G;
+        const uint32_t a = g.X()[i];
+        cios_rowmac<M, R>(y, a, b);
+        const uint32_t q = __shfl_sync(0xffffffffu, y[R % L], g.gbase) * n0i;   // word 0 is thread 0's
+        cios_rowmac<M, R>(y, q, nn);
+        const uint32_t z = __shfl_sync(0xffffffffu, y[R % L], g.gbase + (g.t + 1 < G ? g.t + 1 : 0));
+        y[R % L] = 0u;   // word 0 leaves; this register becomes logical word M+1
+        constexpr int R1 = (R + 1) % L;
+        add_cc(y[(M - 1 + R1) % L], g.t + 1 < G ? z : 0u);
+        addc_cc(y[(M + R1) % L], 0u);
+        addc(y[(M + 1 + R1) % L], 0u);
+        cios_steps<S, R1, CNT - 1>(g, y, i + 1, b, nn, n0i);
+    }
+}
+
+// X <- X * Y * W^-NP (< 2N for inputs < 2N when 4N <= W^NP), returns the word above X
+template <class S>
+MPG_DI uint32_t cios_product(const Grp<S> &g, bool square) {
+    constexpr int G = S::G, M = S::M, NP = S::NP, L = M + 2;
+    static_assert(M % 2 == 0 && M >= 4, "CIOS needs an even M >= 4");
+    uint32_t b[M], nn[M], y[L];
+    lds<M>(b, (square ? g.X() : g.Y()) + g.t * M);
+    lds<M>(nn, g.N() + g.t * M);
+    const uint32_t n0i = g.NI()[0];   // N' mod W = (-N)^-1 mod W
+    zero<L>(y);
+    constexpr int BODIES = NP / L, REM = NP % L;
+    MPG_BLOCK_LOOP
+    for (int k = 0; k < BODIES; ++k) cios_steps<S, 0, L>(g, y, k * L, b, nn, n0i);
+    cios_steps<S, 0, REM>(g, y, BODIES * L, b, nn, n0i);
+    // resolve the carry-save words: thread t-1's two top words sit on this thread's words 0, 1
+    uint32_t lo[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) lo[j] = y[(j + REM) % L];
+    const uint32_t o0 = y[(M + REM) % L], o1 = y[(M + 1 + REM) % L];
+    const int src = g.gbase + (g.t > 0 ? g.t - 1 : 0);
+    const uint32_t i0 = __shfl_sync(0xffffffffu, o0, src), i1 = __shfl_sync(0xffffffffu, o1, src);
+    add_cc(lo[0], g.t > 0 ? i0 : 0u);
+    addc_cc(lo[1], g.t > 0 ? i1 : 0u);
+#pragma unroll
+    for (int j = 2; j < M; ++j) addc_cc(lo[j], 0u);
+    const uint32_t cgen = addc_get();
+    uint32_t all = lo[0];
+#pragma unroll
+    for (int j = 1; j < M; ++j) all &= lo[j];
+    const uint64_t Gm = g.gbits(cgen != 0u), Pm = g.gbits(all == 0xffffffffu);
+    const uint64_t cin = (Pm + (Gm << 1)) ^ Pm;
+    add_word<M>(lo, (uint32_t)(cin >> g.t) & 1u);
+    const uint32_t top = __shfl_sync(0xffffffffu, o0, g.gbase + G - 1) + ((uint32_t)(cin >> G) & 1u);
+    gsync();   // every thread has read X
+    sts<M>(g.X() + g.t * M, lo);
+    gsync();
+    return top;
+}
+
+template <class S>
+MPG_DI void step_cios(const Grp<S> &g, bool square, bool lazy) {
+    const uint32_t top = cios_product<S>(g, square);
+    if (!lazy) cond_sub<S>(g, g.X(), top, g.N(), g.X());
+}
+
 // X <- X * Y * R^-1 mod N (or X^2 * R^-1 when square): X, Y, N, N' in shared memory.
-// Y is overwritten (it holds q afterwards).
+// Y is overwritten (it holds q afterwards). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5),
+// 2 word-serial CIOS (Alg. 4).
 template <class S, int RED>
 MPG_DI void mont_mul(const Grp<S> &g, bool square, bool lazy) {
-    if (square) step_sqr<S>(g);
-    else step_mul<S>(g);
-    step_reduce<S, RED>(g, lazy);
+    if constexpr (RED == 2) {
+        step_cios<S>(g, square, lazy);
+    } else {
+        if (square) step_sqr<S>(g);
+        else step_mul<S>(g);
+        step_reduce<S, RED>(g, lazy);
+    }
 }
 
 }  // namespace mpg

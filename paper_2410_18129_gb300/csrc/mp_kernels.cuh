@@ -368,9 +368,11 @@ template <class S, int TPB>
 struct ShapeImpl {
     static cudaError_t mul(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 0>(k_mul<S, TPB>, A, st); }
     static cudaError_t mont(const KArgs &A, cudaStream_t st) {
+        if (A.red == 2) return launch_k<S, TPB, 5>(k_mont<S, TPB, 2>, A, st);
         return A.red ? launch_k<S, TPB, 3>(k_mont<S, TPB, 1>, A, st) : launch_k<S, TPB, 1>(k_mont<S, TPB, 0>, A, st);
     }
     static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
+        if (A.red == 2) return launch_k<S, TPB, 6>(k_modexp<S, TPB, 2>, A, st);
         return A.red ? launch_k<S, TPB, 4>(k_modexp<S, TPB, 1>, A, st) : launch_k<S, TPB, 2>(k_modexp<S, TPB, 0>, A, st);
     }
     static ShapeOps ops() {

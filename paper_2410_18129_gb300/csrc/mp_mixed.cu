@@ -166,6 +166,7 @@ extern "C" int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_r
                                       size_t workspace_bytes, void *stream) {
     int rc = check_jobs(jobs, njobs);
     if (rc != MP_OK) return rc;
+    if (red == MP_RED_CIOS) return MP_ERR_UNIMPLEMENTED;   // the persistent kernel carries Alg. 5/6 only
     if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
     if (!workspace || ((uintptr_t)workspace & 255u)) return workspace ? MP_ERR_ALIGN : MP_ERR_ARG;
     if (workspace_bytes < modexp_mixed_workspace_bytes(jobs, njobs)) return MP_ERR_NOMEM;

@@ -121,7 +121,7 @@ def test_mont_mul_sqr(mp, bits, layout):
     C = out_tensor(mp, batch, n, layout)
     want_mul = oracle.mont_def(b.a, b.b, b.N)
     want_sqr = oracle.mont_def(b.a, b.a, b.N)
-    for red in (mp.RED_TRUNCATED, mp.RED_FULL):
+    for red in (mp.RED_TRUNCATED, mp.RED_FULL, mp.RED_CIOS):
         mp.mont_mul(C, A, B, ctx, red)
         assert_equal(host(mp, C, batch, n, layout), want_mul, f"mont_mul {bits} red={red}")
         mp.mont_sqr(C, A, ctx, red)
@@ -153,7 +153,7 @@ def test_mont_special_moduli(mp):
     B = len(rows)
     ctx = mp.MontCtx(dev(mp, N, IM), B, bits, IM)
     C = out_tensor(mp, B, n, IM)
-    for red in (0, 1):
+    for red in (0, 1, 2):
         mp.mont_mul(C, dev(mp, a, IM), dev(mp, bb, IM), ctx, red)
         assert_equal(host(mp, C, B, n, IM), oracle.mont_def(a, bb, N), f"special red={red}")
 
@@ -168,7 +168,7 @@ def test_modexp(mp, bits, batch, window, layout):
     ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
     Y = out_tensor(mp, batch, b.n, layout)
     want = oracle.modexp(b.a, b.e, b.ebits, b.N)
-    for red in (0, 1):
+    for red in (0, 1, 2):
         mp.modexp_consttime(Y, dev(mp, b.a, layout), dev(mp, b.e, layout), b.ebits, ctx, window, red)
         assert_equal(host(mp, Y, batch, b.n, layout), want, f"modexp {bits} w={window} red={red}")
 
@@ -192,7 +192,7 @@ def test_modexp_lazy_slack_boundary(mp, bits):
     e = si.from_ints([x[2] for x in rows], n)
     ctx = mp.MontCtx(dev(mp, N, IL), B, bits, IL)
     want = [pow(x[1], x[2], x[0]) for x in rows]
-    for red in (0, 1):
+    for red in (0, 1, 2):
         Y = out_tensor(mp, B, n, IL)
         mp.modexp_consttime(Y, dev(mp, a, IL), dev(mp, e, IL), bits, ctx, 5, red)
         got = host(mp, Y, B, n, IL)
@@ -429,4 +429,7 @@ def test_fixed_base_requests(mp, bits, window):
             (Y2, dev(mp, b2.a, IL), dev(mp, b2.e, IL), 1024, ctx2, 4)]
     mp.modexp_consttime_mixed(jobs, 0, mp.mixed_workspace(jobs))
     assert_equal(host(mp, Y3, nreq, b.n, IL), want, "fixed base in a mixed launch")
+    with pytest.raises(mp.MpError) as err:
+        mp.modexp_consttime_mixed(jobs, mp.RED_CIOS, mp.mixed_workspace(jobs))
+    assert err.value.status == -7
     assert_equal(host(mp, Y2, 19, b2.n, IL), oracle.modexp(b2.a, b2.e, 1024, b2.N), "ordinary job beside it")
