@@ -207,7 +207,9 @@ int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint32_t *exp, u
  * Tuning (process-wide; set it before issuing work, not concurrently with it).
  * Every operand size maps to a size class (its padded word count); a class has one
  * or more compiled group shapes: G threads cooperate on one instance, each holding
- * M words. mp_shape_candidates lists them (default first; returns how many).
+ * M words. mp_shape_candidates lists them (default first; returns how many); G < 0
+ * names the same shape with thread t of every instance in warp t of its block (the lane
+ * is the instance), which makes every branch on the thread index warp-uniform.
  * mp_tune_set selects the shape (G = M = 0 keeps it), the default window width of
  * modexp_consttime for window = 0 (0: built-in rule) and the size from which
  * MP_ALGO_AUTO products use Karatsuba (0: built-in rule) for the class of `bits`.

@@ -19,6 +19,7 @@ ShapeOps shape_ops_16_6();
 ShapeOps shape_ops_8_16();
 ShapeOps shape_ops_16_8();
 ShapeOps shape_ops_8_18();
+ShapeOps shape_ops_8_8_w();
 }  // namespace mpg
 
 using namespace mpg;
@@ -35,7 +36,7 @@ static constexpr uint32_t KARATSUBA_FROM_BITS = 4097;
 struct SizeClass {
     uint32_t np;
     int nshapes;
-    ShapeOps shapes[2];
+    ShapeOps shapes[3];
     int chosen;          // index into shapes
     uint32_t window;     // default window for modexp (0: built-in rule)
     uint32_t kara_from;  // AUTO products use Karatsuba from this many bits (0: built-in rule)
@@ -48,7 +49,7 @@ static void init_classes() {
     g_classes[0] = SizeClass{8, 1, {shape_ops_2_4()}, 0, 0, 0};
     g_classes[1] = SizeClass{16, 1, {shape_ops_4_4()}, 0, 0, 0};
     g_classes[2] = SizeClass{32, 2, {shape_ops_4_8(), shape_ops_8_4()}, 0, 0, 0};
-    g_classes[3] = SizeClass{64, 2, {shape_ops_8_8(), shape_ops_16_4()}, 0, 0, 0};
+    g_classes[3] = SizeClass{64, 3, {shape_ops_8_8(), shape_ops_16_4(), shape_ops_8_8_w()}, 0, 0, 0};
     g_classes[4] = SizeClass{96, 2, {shape_ops_8_12(), shape_ops_16_6()}, 0, 0, 0};
     g_classes[5] = SizeClass{128, 2, {shape_ops_16_8(), shape_ops_8_16()}, 0, 0, 0};   // 16x8 measured faster
     g_classes[6] = SizeClass{144, 1, {shape_ops_8_18()}, 0, 0, 0};
@@ -66,6 +67,17 @@ static SizeClass *class_for(uint32_t n) {
 static const ShapeOps *shape_for(uint32_t n) {
     SizeClass *c = class_for(n);
     return c ? &c->shapes[c->chosen] : nullptr;
+}
+
+// the shape for a Montgomery product with reduction `red`: CIOS passes a word between the
+// threads of an instance at every step, so it runs on a lane-mapped shape of the class
+static const ShapeOps *shape_for_red(uint32_t n, int red) {
+    SizeClass *c = class_for(n);
+    if (!c) return nullptr;
+    if (red == MP_RED_CIOS && c->shapes[c->chosen].G < 0)
+        for (int i = 0; i < c->nshapes; ++i)
+            if (c->shapes[i].G > 0) return &c->shapes[i];
+    return &c->shapes[c->chosen];
 }
 
 
@@ -374,7 +386,7 @@ static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, cons
     KArgs A{};
     fill_ctx_args(A, c);
     A.out = out; A.a = a; A.b = square ? a : b; A.red = (int)red; A.square = square ? 1 : 0;
-    return cuda_status(shape_for(c->np)->mont(A, S(stream)));
+    return cuda_status(shape_for_red(c->np, (int)red)->mont(A, S(stream)));
 }
 
 extern "C" int mont_mul(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
@@ -475,7 +487,7 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     A.out = y; A.a = base; A.e = exp; A.table = reinterpret_cast<uint32_t *>(ws);
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
-    int rc = cuda_status(shape_for(c->np)->modexp(A, st));
+    int rc = cuda_status(shape_for_red(c->np, (int)red)->modexp(A, st));
     if (own) {
         if (cudaFreeAsync(ws, st) != cudaSuccess && rc == MP_OK) rc = MP_ERR_CUDA;
     }
@@ -500,7 +512,7 @@ extern "C" int modexp_table_build(void *tables, size_t bytes, const uint32_t *ba
     fill_ctx_args(A, c);
     A.a = base; A.table = reinterpret_cast<uint32_t *>(tables); A.window = (int)window; A.red = (int)red;
     A.mode = 1;
-    return cuda_status(shape_for(c->np)->modexp(A, S(stream)));
+    return cuda_status(shape_for_red(c->np, (int)red)->modexp(A, S(stream)));
 }
 
 extern "C" int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint32_t *exp, uint32_t exp_bits,
@@ -518,7 +530,7 @@ extern "C" int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint3
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
     A.mode = 2;
-    return cuda_status(shape_for(c->np)->modexp(A, S(stream)));
+    return cuda_status(shape_for_red(c->np, (int)red)->modexp(A, S(stream)));
 }
 
 // ------------------------------------------------------------------ exponentiation without allocation
@@ -573,5 +585,5 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
     A.out = y; A.a = base; A.e = exp; A.table = tables;
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
-    return cuda_status(shape_for(c->np)->modexp(A, S(stream)));
+    return cuda_status(shape_for_red(c->np, (int)red)->modexp(A, S(stream)));
 }

@@ -26,12 +26,23 @@
 // loops over block products stay loops: one copy of the block product per phase
 #define MPG_BLOCK_LOOP _Pragma("unroll 1")
 
+// block-wide barrier of the warp mapping (a checking build may supply its own)
+#ifndef MPG_BLOCK_BARRIER
+#define MPG_BLOCK_BARRIER() __syncthreads()
+#endif
+
 namespace mpg {
 
-template <int G_, int M_>
+// W_ = false: the G threads of an instance are G consecutive lanes of a warp (a warp holds
+// 32/G instances). W_ = true: thread t of an instance is warp t of its block and the lane is
+// the instance (a block of G warps holds 32 instances), so every branch on the thread index
+// is uniform across a warp; the threads of an instance then talk through shared memory and
+// block barriers instead of shuffles and ballots.
+template <int G_, int M_, bool W_ = false>
 struct Shape {
     static constexpr int G = G_;           // threads per instance
     static constexpr int M = M_;           // words per thread
+    static constexpr bool WMAP = W_;       // thread index = warp index (see above)
     static constexpr int NP = G * M;       // words per operand (padded size)
     static constexpr int H = M / 2;        // half-block width of the truncated products
     static constexpr int A1 = 2 * M + 2;   // slot accumulator words, full blocks
@@ -47,8 +58,12 @@ struct Shape {
     static constexpr int OFF_T = 4 * NP;          // T (2*NP words)
     static constexpr int OFF_P = 6 * NP;          // slot spills: 2G slots of M+2 words
     static constexpr int OFF_Z = OFF_P + 2 * G * (M + 2);   // M zero words
-    static constexpr int WORDS_RAW = OFF_Z + M;
-    static constexpr int WORDS = (WORDS_RAW + 3) & ~3;  // keep every instance 16-byte aligned
+    static constexpr int OFF_XB = OFF_Z + M;      // W_: one byte per thread (predicate exchange)
+    static constexpr int OFF_XW = OFF_XB + (W_ ? (G + 3) / 4 : 0);   // W_: one broadcast word
+    static constexpr int WORDS_RAW = OFF_XW + (W_ ? 1 : 0);
+    // keep every instance 16-byte aligned; with W_, 32 lanes read the same offset of 32
+    // instances: a stride of 4 (mod 8) words puts 8 lanes' 16-byte loads on distinct banks
+    static constexpr int WORDS = W_ ? ((WORDS_RAW + 3) / 8) * 8 + 4 : (WORDS_RAW + 3) & ~3;
 };
 
 // Per-thread view of its group.
@@ -58,7 +73,7 @@ struct Grp {
     uint32_t *pa;   // slot spill area (2G slots of M+2 words)
     uint32_t *za;   // M zero words
     int t;          // thread index in the group
-    int gbase;      // warp lane of thread 0 of the group
+    int gbase;      // warp lane of thread 0 of the group (lane mapping)
     MPG_DI uint32_t *X() const { return sm + S::OFF_X; }
     MPG_DI uint32_t *Y() const { return sm + S::OFF_Y; }
     MPG_DI uint32_t *Q() const { return sm + S::OFF_Y; }   // q reuses Y once T is formed
@@ -67,9 +82,55 @@ struct Grp {
     MPG_DI uint32_t *T() const { return sm + S::OFF_T; }
     MPG_DI uint32_t *P() const { return pa; }
     MPG_DI uint32_t *Z() const { return za; }
-    // this group's bits of a warp ballot
+    // all threads of the group reach this point (and see each other's shared-memory writes)
+    MPG_DI void sync() const {
+        if constexpr (S::WMAP) MPG_BLOCK_BARRIER();
+        else __syncwarp();
+    }
+    // m[k] bit u = p[k] of thread u of the group (collective: every thread calls it)
+    template <int K>
+    MPG_DI void bits(const bool (&p)[K], uint32_t (&m)[K]) const {
+        static_assert(K <= 8, "at most 8 predicates");
+        if constexpr (!S::WMAP) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) m[k] = (__ballot_sync(0xffffffffu, p[k]) >> gbase) & ((1u << S::G) - 1u);
+        } else {
+            uint32_t b = 0u;
+#pragma unroll
+            for (int k = 0; k < K; ++k) b |= (p[k] ? 1u : 0u) << k;
+            reinterpret_cast<uint8_t *>(sm + S::OFF_XB)[t] = (uint8_t)b;
+            MPG_BLOCK_BARRIER();
+            constexpr int NW = (S::G + 3) / 4;
+            uint32_t w[NW];
+#pragma unroll
+            for (int i = 0; i < NW; ++i) w[i] = sm[S::OFF_XB + i];
+#pragma unroll
+            for (int k = 0; k < K; ++k) m[k] = 0u;
+#pragma unroll
+            for (int u = 0; u < S::G; ++u) {
+                const uint32_t byte = w[u >> 2] >> (8 * (u & 3));
+#pragma unroll
+                for (int k = 0; k < K; ++k) m[k] |= ((byte >> k) & 1u) << u;
+            }
+            MPG_BLOCK_BARRIER();   // the exchange byte may be written again
+        }
+    }
+    // the group's mask of one predicate (lane mapping only: a single ballot)
     MPG_DI uint32_t gbits(bool pred) const {
+        static_assert(!S::WMAP, "use bits<K>() with the warp mapping");
         return (__ballot_sync(0xffffffffu, pred) >> gbase) & ((1u << S::G) - 1u);
+    }
+    // thread src's value v, for every thread of the group (collective)
+    MPG_DI uint32_t bcast(uint32_t v, int src) const {
+        if constexpr (!S::WMAP) {
+            return __shfl_sync(0xffffffffu, v, gbase + src);
+        } else {
+            if (t == src) sm[S::OFF_XW] = v;
+            MPG_BLOCK_BARRIER();
+            const uint32_t r = sm[S::OFF_XW];
+            MPG_BLOCK_BARRIER();
+            return r;
+        }
     }
 };
 
@@ -253,7 +314,7 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
         for (int j = 0; j < B; ++j) lo[k][j] = V[j];
         if (s == NSLOT - 1) top = V[B];
     }
-    if constexpr (XF::active) gsync();
+    if constexpr (XF::active) g.sync();
     // 2. add the predecessor's spill
     uint32_t ov[2][2];
 #pragma unroll
@@ -279,7 +340,24 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
     }
     // 3. add the predecessor's overflow: leaves a 0/1 carry per slot
     uint32_t oin[2][2];
-    pred_overflow<G, PAT>(g.t, g.gbase, ov[0], ov[1], oin[0], oin[1]);
+    if constexpr (!S::WMAP) {
+        pred_overflow<G, PAT>(g.t, g.gbase, ov[0], ov[1], oin[0], oin[1]);
+    } else {   // through the spill words, which every thread has read by now
+        g.sync();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int s = slot_of<G, PAT>(g.t, k);
+            Pm[s * SP] = ov[k][0];
+            Pm[s * SP + 1] = ov[k][1];
+        }
+        g.sync();
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int s = slot_of<G, PAT>(g.t, k);
+            oin[k][0] = s ? Pm[(s - 1) * SP] : 0u;
+            oin[k][1] = s ? Pm[(s - 1) * SP + 1] : 0u;
+        }
+    }
     uint32_t cgen[2], cprop[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -294,12 +372,13 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
         cprop[k] = (all == 0xffffffffu) ? 1u : 0u;
     }
     // 4. carry-lookahead over the slots: carry into slot s = bit s of ((P + 2G) ^ P)
-    const uint32_t gA = g.gbits(cgen[0] != 0u), pA = g.gbits(cprop[0] != 0u);
-    const uint32_t gB = g.gbits(cgen[1] != 0u), pB = g.gbits(cprop[1] != 0u);
-    const uint64_t Gm = slot_mask<G, PAT>(gA, gB);
-    const uint64_t Pmask = slot_mask<G, PAT>(pA, pB);
+    const bool pr[4] = {cgen[0] != 0u, cprop[0] != 0u, cgen[1] != 0u, cprop[1] != 0u};
+    uint32_t mk[4];
+    g.template bits<4>(pr, mk);
+    const uint64_t Gm = slot_mask<G, PAT>(mk[0], mk[2]);
+    const uint64_t Pmask = slot_mask<G, PAT>(mk[1], mk[3]);
     const uint64_t cin = (Pmask + (Gm << 1)) ^ Pmask;
-    gsync();   // every lane has read the spills it needs before OUT and P change again
+    g.sync();   // every thread has read the spills it needs before OUT and P change again
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int s = slot_of<G, PAT>(g.t, k);
@@ -308,8 +387,8 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
     }
     // the carry out of the last slot; callers use it only where the value above it is 0 or 1
     constexpr int owner = (PAT == PAT_ZIGZAG) ? 0 : G - 1;
-    top = __shfl_sync(0xffffffffu, top, g.gbase + owner);
-    gsync();
+    top = g.bcast(top, owner);
+    g.sync();
     return top + ((uint32_t)(cin >> NSLOT) & 1u);
 }
 
@@ -322,15 +401,24 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
     constexpr int G = S::G, M = S::M, A = S::A1;
     uint32_t V[A];
     zero<A>(V);
-    MPG_BLOCK_LOOP
-    for (int j = 0; j < G; ++j) {
-        const int v = (g.t - j) & (G - 1);
-        mac_block<M>(V, X + j * M, Y + v * M);
-        if (j == g.t) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+    const int t = g.t;
+    if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
+        MPG_BLOCK_LOOP
+        for (int j = 0; j <= t; ++j) mac_block<M>(V, X + j * M, Y + (t - j) * M);
+        flush<M>(V, T + t * M, g.P() + t * (M + 2));
+        MPG_BLOCK_LOOP
+        for (int j = t + 1; j < G; ++j) mac_block<M>(V, X + j * M, Y + (t - j + G) * M);
+    } else {
+        MPG_BLOCK_LOOP
+        for (int j = 0; j < G; ++j) {
+            const int v = (t - j) & (G - 1);
+            mac_block<M>(V, X + j * M, Y + v * M);
+            if (j == t) park<M>(V, T + t * M, g.P() + t * (M + 2));
+        }
+        unpark_sub<M>(V, T + t * M, g.P() + t * (M + 2));
     }
-    unpark_sub<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
-    park<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
-    gsync();
+    park<M>(V, T + (G + t) * M, g.P() + (G + t) * (M + 2));
+    g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
     resolve<S, M, PAT_SEQ>(g, in0, NoXform{}, T);
@@ -370,24 +458,35 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     constexpr int K = G / 2;                    // max of nA + nB over the group
     uint32_t V[A];
     zero<A>(V);
-    MPG_BLOCK_LOOP
-    for (int j = 0; j < K; ++j) {
-        if (j == nA) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
-        int u, v;
-        if (j < nA) { u = j; v = g.t - j; }
-        else { u = g.t + 1 + (j - nA); v = G + g.t - u; }
-        const bool live = j < nA + nB;
-        mac_block<M>(V, X + (live ? u : 0) * M, live ? X + v * M : g.Z());
+    if constexpr (S::WMAP) {   // t is uniform across the warp: exact pair counts, no dummy blocks
+        MPG_BLOCK_LOOP
+        for (int j = 0; j < nA; ++j) mac_block<M>(V, X + j * M, X + (g.t - j) * M);
+        flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+        MPG_BLOCK_LOOP
+        for (int j = 0; j < nB; ++j) {
+            const int u = g.t + 1 + j;
+            mac_block<M>(V, X + u * M, X + (G + g.t - u) * M);
+        }
+    } else {
+        MPG_BLOCK_LOOP
+        for (int j = 0; j < K; ++j) {
+            if (j == nA) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+            int u, v;
+            if (j < nA) { u = j; v = g.t - j; }
+            else { u = g.t + 1 + (j - nA); v = G + g.t - u; }
+            const bool live = j < nA + nB;
+            mac_block<M>(V, X + (live ? u : 0) * M, live ? X + v * M : g.Z());
+        }
+        if (nA == K) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+        unpark_sub<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
     }
-    if (nA == K) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
-    unpark_sub<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
     park<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
     uint32_t x[M], P[2 * M];
     lds<M>(x, X + g.t * M);
-    gsync();                                    // all reads of X are done
+    g.sync();                                   // all reads of X are done
     block_sqr<M>(P, x);
     sts<2 * M>(D + 2 * g.t * M, P);
-    gsync();
+    g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
     resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{D}, T);
@@ -401,17 +500,26 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
     constexpr int G = S::G, H = S::H, A = S::A2;
     uint32_t V[A];
     zero<A>(V);
-    MPG_BLOCK_LOOP
-    for (int j = 0; j <= 2 * G; ++j) {
-        int u, v;
-        if (j <= g.t) { u = j; v = g.t - j; }
-        else { u = j - g.t - 1; v = 2 * G - j; }
-        mac_block<H>(V, X + u * H, Y + v * H);
-        if (j == g.t) park<H>(V, Q + g.t * H, g.P() + g.t * (H + 2));
+    const int t = g.t;
+    if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
+        MPG_BLOCK_LOOP
+        for (int j = 0; j <= t; ++j) mac_block<H>(V, X + j * H, Y + (t - j) * H);
+        flush<H>(V, Q + t * H, g.P() + t * (H + 2));
+        MPG_BLOCK_LOOP
+        for (int j = t + 1; j <= 2 * G; ++j) mac_block<H>(V, X + (j - t - 1) * H, Y + (2 * G - j) * H);
+    } else {
+        MPG_BLOCK_LOOP
+        for (int j = 0; j <= 2 * G; ++j) {
+            int u, v;
+            if (j <= t) { u = j; v = t - j; }
+            else { u = j - t - 1; v = 2 * G - j; }
+            mac_block<H>(V, X + u * H, Y + v * H);
+            if (j == t) park<H>(V, Q + t * H, g.P() + t * (H + 2));
+        }
+        unpark_sub<H>(V, Q + t * H, g.P() + t * (H + 2));
     }
-    unpark_sub<H>(V, Q + g.t * H, g.P() + g.t * (H + 2));
-    park<H>(V, Q + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
-    gsync();
+    park<H>(V, Q + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
+    g.sync();
     uint32_t in0[H + 2];
     zero<H + 2>(in0);
     resolve<S, H, PAT_ZIGZAG>(g, in0, NoXform{}, Q);
@@ -496,27 +604,58 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
         const uint32_t yn = live ? Ns[(2 * G - 2 - u) * H + H - 1] : 0u;
         add_word<H + 3>(Z, __umulhi(xq, yn));
     }
+    if constexpr (S::WMAP) {   // park Z in T's low half, dead since q was formed (T[NP-1] kept)
+        static_assert(G * (H + 3) <= NP - 1, "Z exchange must stay below word NP-1 of T");
+        uint32_t *zs = g.T() + g.t * (H + 3);
+#pragma unroll
+        for (int k = 0; k < H + 3; ++k) zs[k] = Z[k];
+    }
     // output slots: A = t (absolute 2G+t), B = 2G-1-t (absolute 4G-1-t)
     uint32_t V[A];
     zero<A>(V);
-    const int nA = 2 * G - 1 - g.t;
-    MPG_BLOCK_LOOP
-    for (int j = 0; j < 2 * G - 1; ++j) {
-        int u, v;
-        if (j < nA) { u = g.t + 1 + j; v = 2 * G + g.t - u; }
-        else { u = j + 1; v = 4 * G - 2 - g.t - j; }
-        mac_block<H>(V, Qs + u * H, Ns + v * H);
-        if (j == nA - 1) park<H>(V, C + g.t * H, g.P() + g.t * (H + 2));
+    const int t = g.t;
+    const int nA = 2 * G - 1 - t;
+    if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
+        MPG_BLOCK_LOOP
+        for (int j = 0; j < nA; ++j) {
+            const int u = t + 1 + j;
+            mac_block<H>(V, Qs + u * H, Ns + (2 * G + t - u) * H);
+        }
+        flush<H>(V, C + t * H, g.P() + t * (H + 2));
+        MPG_BLOCK_LOOP
+        for (int j = nA; j < 2 * G - 1; ++j) mac_block<H>(V, Qs + (j + 1) * H, Ns + (4 * G - 2 - t - j) * H);
+    } else {
+        MPG_BLOCK_LOOP
+        for (int j = 0; j < 2 * G - 1; ++j) {
+            int u, v;
+            if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
+            else { u = j + 1; v = 4 * G - 2 - t - j; }
+            mac_block<H>(V, Qs + u * H, Ns + v * H);
+            if (j == nA - 1) park<H>(V, C + t * H, g.P() + t * (H + 2));
+        }
+        unpark_sub<H>(V, C + t * H, g.P() + t * (H + 2));
     }
-    unpark_sub<H>(V, C + g.t * H, g.P() + g.t * (H + 2));
-    park<H>(V, C + (2 * G - 1 - g.t) * H, g.P() + (2 * G - 1 - g.t) * (H + 2));
-    // sum Z over the group (butterfly; every lane gets the total)
+    park<H>(V, C + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
+    if constexpr (S::WMAP) {
+        // thread 0 (owner of slot 0, the only one that needs the sum) adds the parked Z's
+        g.sync();
+        if (t == 0) {
+#pragma unroll 1
+            for (int u = 1; u < G; ++u) {
+                uint32_t o[H + 3];
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-        uint32_t o[H + 3];
+                for (int k = 0; k < H + 3; ++k) o[k] = g.T()[u * (H + 3) + k];
+                add_n<H + 3>(Z, o);
+            }
+        }
+    } else {   // sum Z over the group (butterfly; every lane gets the total)
 #pragma unroll
-        for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
-        add_n<H + 3>(Z, o);
+        for (int off = G / 2; off > 0; off >>= 1) {
+            uint32_t o[H + 3];
+#pragma unroll
+            for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
+            add_n<H + 3>(Z, o);
+        }
     }
     // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
     const uint32_t L = ~T[NP - 1] + low_zero;
@@ -525,7 +664,7 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
 #pragma unroll
     for (int j = 0; j < H + 2; ++j) in0[j] = Z[1 + j];
     add_word<H + 2>(in0, extra + c_add);
-    gsync();
+    g.sync();
     return resolve<S, H, PAT_ZIGZAG>(g, in0, AddendXform<H>{T + NP}, C);
 }
 
@@ -548,7 +687,7 @@ MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *N
     }
     addT(G + g.t, V);
     flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
-    gsync();
+    g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
     return resolve<S, M, PAT_SEQ>(g, in0, NoXform{}, T);
@@ -566,7 +705,10 @@ MPG_DI void cond_sub(const Grp<S> &g, const uint32_t *C, uint32_t carry, const u
 #pragma unroll
     for (int j = 0; j < M; ++j) { d[j] = c[j]; eq |= c[j] ^ nn[j]; }
     const uint32_t bgen = sub_n<M>(d, nn);
-    const uint32_t gb = g.gbits(bgen != 0u), pb = g.gbits(eq == 0u);
+    const bool pr[2] = {bgen != 0u, eq == 0u};
+    uint32_t mk[2];
+    g.template bits<2>(pr, mk);
+    const uint32_t gb = mk[0], pb = mk[1];
     const uint64_t Pm = pb, Gm = gb;
     const uint64_t bin = (Pm + (Gm << 1)) ^ Pm;
     sub_word<M>(d, (uint32_t)(bin >> g.t) & 1u);
@@ -575,9 +717,9 @@ MPG_DI void cond_sub(const Grp<S> &g, const uint32_t *C, uint32_t carry, const u
     const uint32_t msk = 0u - ge;
 #pragma unroll
     for (int j = 0; j < M; ++j) c[j] = (d[j] & msk) | (c[j] & ~msk);
-    gsync();
+    g.sync();
     sts<M>(OUT + g.t * M, c);
-    gsync();
+    g.sync();
 }
 
 // Steps of a Montgomery product. The kernels call the product from exactly one
@@ -607,8 +749,11 @@ MPG_DI void step_reduce(Grp<S> g, bool lazy) {
             if (g.t * M + j < NP - 1) nz_low |= x[j];
         }
     }
-    const uint32_t c_add = g.gbits(nz_all != 0u) ? 1u : 0u;
-    const uint32_t low_zero = g.gbits(nz_low != 0u) ? 0u : 1u;
+    const bool pr[2] = {nz_all != 0u, nz_low != 0u};
+    uint32_t mk[2];
+    g.template bits<2>(pr, mk);
+    const uint32_t c_add = mk[0] ? 1u : 0u;
+    const uint32_t low_zero = mk[1] ? 0u : 1u;
     phase_mullo<S>(g, T, g.NI(), g.Q());
     if constexpr (RED == 0) {
         const uint32_t carry = phase_mulhi<S>(g, g.Q(), g.N(), T, c_add, low_zero, g.X());
@@ -623,7 +768,7 @@ MPG_DI void step_reduce(Grp<S> g, bool lazy) {
             uint32_t x[M];
             lds<M>(x, T + NP + g.t * M);
             sts<M>(g.X() + g.t * M, x);
-            gsync();
+            g.sync();
         }
     }
 }
@@ -689,6 +834,7 @@ template <class S>
 MPG_DI uint32_t cios_product(const Grp<S> &g, bool square) {
     constexpr int G = S::G, M = S::M, NP = S::NP, L = M + 2;
     static_assert(M % 2 == 0 && M >= 4, "CIOS needs an even M >= 4");
+    static_assert(!S::WMAP, "CIOS passes a word between threads at every step: lane mapping only");
     uint32_t b[M], nn[M], y[L];
     lds<M>(b, (square ? g.X() : g.Y()) + g.t * M);
     lds<M>(nn, g.N() + g.t * M);

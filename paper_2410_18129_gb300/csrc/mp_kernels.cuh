@@ -92,16 +92,34 @@ struct KArgs {
     int lazy;                // exponentiation: 4N <= W^NP, products skip the final subtraction (results < 2N)
 };
 
+// instance of this thread within its block, and its thread index within the instance
+template <class S>
+MPG_DI int local_instance() {
+    if constexpr (S::WMAP) return (int)(threadIdx.x & 31);   // lane = instance, warp = thread
+    else return (int)(threadIdx.x / S::G);                   // G consecutive lanes per instance
+}
+
 template <class S>
 MPG_DI Grp<S> make_group(uint32_t *smem) {
     Grp<S> g;
-    const int gi = threadIdx.x / S::G;
-    g.sm = smem + gi * S::WORDS;
+    g.sm = smem + local_instance<S>() * S::WORDS;
     g.pa = g.sm + S::OFF_P;
     g.za = g.sm + S::OFF_Z;
-    g.t = threadIdx.x % S::G;
-    g.gbase = (threadIdx.x & 31) & ~(S::G - 1);
+    if constexpr (S::WMAP) {
+        g.t = (int)(threadIdx.x >> 5);
+        g.gbase = 0;
+    } else {
+        g.t = threadIdx.x % S::G;
+        g.gbase = (threadIdx.x & 31) & ~(S::G - 1);
+    }
     return g;
+}
+
+// instances per block: TPB/G either way (with the warp mapping a block is G warps = 32 instances)
+template <class S, int TPB>
+MPG_DI size_t global_instance() {
+    static_assert(!S::WMAP || TPB == 32 * S::G, "warp mapping: one block = G warps");
+    return (size_t)blockIdx.x * (TPB / S::G) + local_instance<S>();
 }
 
 template <class S>
@@ -146,12 +164,12 @@ template <class S, int TPB>
 __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mul(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
-    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    const size_t k = global_instance<S, TPB>();
     const bool valid = k < A.batch;
     init_zero_block<S>(g);
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
-    gsync();
+    g.sync();
     if (A.square) phase_sqr<S>(g, g.X(), g.X(), g.T());   // squares in X, Y
     else phase_mul<S>(g, g.X(), g.Y(), g.T());
     // store 2n words
@@ -166,20 +184,20 @@ template <class S, int TPB, int RED>
 __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mont(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
-    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    const size_t k = global_instance<S, TPB>();
     const bool valid = k < A.batch;
     init_zero_block<S>(g);
     load_ctx<S>(g, g.N(), A.N, A, k, valid);
     load_ctx<S>(g, g.NI(), A.NI, A, k, valid);
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
-    gsync();
+    g.sync();
     // one call site; a second product when the internal radix W^NP differs from the
     // API radix W^n: multiply by W^(2NP-n) mod N
     for (int r = 0; r <= (A.correct ? 1 : 0); ++r) {
         if (r) {
             load_ctx<S>(g, g.Y(), A.K, A, k, valid);
-            gsync();
+            g.sync();
         }
         mont_mul<S, RED>(g, r == 0 && A.square != 0, false);
     }
@@ -276,7 +294,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     } else {
         load_ctx<S>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form
     }
-    gsync();
+    g.sync();
     for (int op = 0; op < nbuild + nwin; ++op) {
         bool square = false;
         if (op >= nbuild) {
@@ -287,7 +305,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
                 zero<M>(x);
                 if (g.t == 0) x[0] = 1u;
                 sts<M>(g.Y() + g.t * M, x);
-                gsync();
+                g.sync();
             } else if (s < w) {
                 square = true;
             } else {   // masked scan of the whole table: every entry is read, one is kept
@@ -302,7 +320,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
                     for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
                 }
                 sts<M>(g.Y() + g.t * M, acc);
-                gsync();
+                g.sync();
             }
         }
         mont_mul<S, RED>(g, square, A.lazy != 0);
@@ -319,7 +337,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
             } else if (A.mode == 0) {
                 load_ctx<S>(g, g.X(), A.R1, A, kc, valid);   // Y_acc = 1 in Montgomery form
             }
-            gsync();
+            g.sync();
         }
     }
     if (A.mode == 1) return;
@@ -333,7 +351,7 @@ template <class S, int TPB, int RED>
 __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_modexp(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
-    const size_t k = (size_t)blockIdx.x * (TPB / S::G) + threadIdx.x / S::G;
+    const size_t k = global_instance<S, TPB>();
     modexp_group<S, RED>(g, A, k);
 }
 
@@ -368,15 +386,25 @@ template <class S, int TPB>
 struct ShapeImpl {
     static cudaError_t mul(const KArgs &A, cudaStream_t st) { return launch_k<S, TPB, 0>(k_mul<S, TPB>, A, st); }
     static cudaError_t mont(const KArgs &A, cudaStream_t st) {
-        if (A.red == 2) return launch_k<S, TPB, 5>(k_mont<S, TPB, 2>, A, st);
+        if constexpr (S::WMAP) {   // CIOS runs on the lane-mapped shapes only (the API picks one)
+            if (A.red == 2) return cudaErrorNotSupported;
+        } else {
+            if (A.red == 2) return launch_k<S, TPB, 5>(k_mont<S, TPB, 2>, A, st);
+        }
         return A.red ? launch_k<S, TPB, 3>(k_mont<S, TPB, 1>, A, st) : launch_k<S, TPB, 1>(k_mont<S, TPB, 0>, A, st);
     }
     static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
-        if (A.red == 2) return launch_k<S, TPB, 6>(k_modexp<S, TPB, 2>, A, st);
+        if constexpr (S::WMAP) {
+            if (A.red == 2) return cudaErrorNotSupported;
+        } else {
+            if (A.red == 2) return launch_k<S, TPB, 6>(k_modexp<S, TPB, 2>, A, st);
+        }
         return A.red ? launch_k<S, TPB, 4>(k_modexp<S, TPB, 1>, A, st) : launch_k<S, TPB, 2>(k_modexp<S, TPB, 0>, A, st);
     }
     static ShapeOps ops() {
-        return ShapeOps{S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont, &modexp, nullptr};
+        // the warp-mapped variant of a shape reports G < 0 (see mp_shape_candidates)
+        return ShapeOps{S::WMAP ? -S::G : S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont,
+                        &modexp, nullptr};
     }
 };
 
@@ -385,6 +413,13 @@ struct ShapeImpl {
 #define MPG_DEFINE_SHAPE(G, M, TPB)                                              \
     namespace mpg {                                                              \
     ShapeOps shape_ops_##G##_##M() { return ShapeImpl<Shape<G, M>, TPB>::ops(); } \
+    }
+
+// the warp-mapped variant of shape (G, M): thread t of each instance is warp t of a block of G
+// warps, lane = instance (32 instances per block)
+#define MPG_DEFINE_SHAPE_W(G, M)                                                                          \
+    namespace mpg {                                                                                       \
+    ShapeOps shape_ops_##G##_##M##_w() { return ShapeImpl<Shape<G, M, true>, 32 * G>::ops(); }           \
     }
 
 // a shape whose products can also run as one level of Karatsuba over the half shape (G, MH)

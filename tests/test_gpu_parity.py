@@ -398,6 +398,52 @@ def test_tuning_round_trip(mp):
         mp.tune_set(bits, before["G"], before["M"], 0)
 
 
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_warp_mapped_shape(mp, layout):
+    """The 2048-bit class's warp-mapped shape (thread t of every instance in warp t of a block,
+    the lane is the instance): every entry point, several blocks plus a ragged one, extreme
+    operands, all reductions (CIOS runs on a lane-mapped shape of the class)."""
+    bits, batch = 2048, 77
+    cands = mp.shape_candidates(bits)
+    assert (-8, 8) in cands
+    before = mp.tune_get(bits)
+    mp.tune_set(bits, -8, 8, 5)
+    try:
+        b = si.make_batch(0, "test", batch, bits, sub=4242)
+        b.a[3] = b.N[3] - np.array([1] + [0] * (b.n - 1), np.uint32)       # N-1
+        b.a[4] = 0
+        b.e[5] = 0
+        n = b.n
+        A, Bv, E = dev(mp, b.a, layout), dev(mp, b.b, layout), dev(mp, b.e, layout)
+        C2 = torch.zeros(mp.array_words(layout, batch, 2 * n), dtype=torch.int32, device="cuda")
+        mp.mp_mul(C2, A, Bv, batch, bits, layout, mp.ALGO_SCHOOLBOOK)
+        assert_equal(host(mp, C2, batch, 2 * n, layout), oracle.mul(b.a, b.b), "mp_mul")
+        mp.mp_sqr(C2, A, batch, bits, layout, mp.ALGO_SCHOOLBOOK)
+        assert_equal(host(mp, C2, batch, 2 * n, layout), oracle.sqr(b.a), "mp_sqr")
+        ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
+        C = out_tensor(mp, batch, n, layout)
+        want_mul, want_sqr = oracle.mont_def(b.a, b.b, b.N), oracle.mont_def(b.a, b.a, b.N)
+        want_exp = oracle.modexp(b.a, b.e, bits, b.N)
+        for red in (0, 1, 2):
+            mp.mont_mul(C, A, Bv, ctx, red)
+            assert_equal(host(mp, C, batch, n, layout), want_mul, f"mont_mul red={red}")
+            mp.mont_sqr(C, A, ctx, red)
+            assert_equal(host(mp, C, batch, n, layout), want_sqr, f"mont_sqr red={red}")
+            Y = out_tensor(mp, batch, n, layout)
+            mp.modexp_consttime(Y, A, E, bits, ctx, 5, red)
+            assert_equal(host(mp, Y, batch, n, layout), want_exp, f"modexp red={red}")
+        if layout == IL:
+            tables = torch.empty(mp.modexp_table_bytes(ctx, 5) // 4, dtype=torch.int32, device="cuda")
+            mp.modexp_table_build(tables, A, ctx, 5)
+            index = np.arange(batch, dtype=np.uint32)[::-1].copy()
+            Y = out_tensor(mp, batch, n, IL)
+            mp.modexp_fixed_base(Y, mp.to_device(index), dev(mp, b.e[index], IL), bits, batch, ctx, tables, 5)
+            assert_equal(host(mp, Y, batch, n, IL), want_exp[index], "fixed base")
+        ctx.free()
+    finally:
+        mp.tune_set(bits, before["G"], before["M"], 0)
+
+
 # ------------------------------------------------------------------ resident tables, fixed bases
 
 @pytest.mark.parametrize("bits,window", [(1024, 4), (2048, 5), (3072, 5), (4096, 6)])
