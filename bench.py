@@ -413,7 +413,8 @@ def bench_4096(args):
         n = b.n
         A, Bv = mp.to_device(mp.interleave(b.a)), mp.to_device(mp.interleave(b.b))
         C = torch.zeros(mp.array_words(IL, B, 2 * n), dtype=torch.int32, device="cuda")
-        for algo, nm in ((mp.ALGO_SCHOOLBOOK, "schoolbook"), (mp.ALGO_KARATSUBA, "karatsuba")):
+        for algo, nm in ((mp.ALGO_SCHOOLBOOK, "schoolbook"), (mp.ALGO_KARATSUBA, "karatsuba"),
+                         (mp.ALGO_KARATSUBA2, "karatsuba2")):
             for op in ("mul", "sqr"):
                 f = (lambda: mp.mp_mul(C, A, Bv, B, bits, IL, algo)) if op == "mul" else \
                     (lambda: mp.mp_sqr(C, A, B, bits, IL, algo))

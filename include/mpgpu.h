@@ -52,7 +52,9 @@ typedef enum {
 } mp_status;
 
 typedef enum { MP_LAYOUT_INSTANCE_MAJOR = 0, MP_LAYOUT_INTERLEAVED = 1 } mp_layout;
-typedef enum { MP_ALGO_AUTO = 0, MP_ALGO_SCHOOLBOOK = 1, MP_ALGO_KARATSUBA = 2 } mp_algo;
+/* Products: schoolbook (Alg. 1/2), one level of Karatsuba (Sec. 3), two levels (mp_mul and
+   mp_sqr of the 4096- and 4608-bit classes only; 9 quarter products instead of 16). */
+typedef enum { MP_ALGO_AUTO = 0, MP_ALGO_SCHOOLBOOK = 1, MP_ALGO_KARATSUBA = 2, MP_ALGO_KARATSUBA2 = 3 } mp_algo;
 /* Reductions: truncated (Alg. 6), classical (Alg. 3/5), word-serial CIOS (Alg. 4). */
 typedef enum { MP_RED_TRUNCATED = 0, MP_RED_FULL = 1, MP_RED_CIOS = 2 } mp_red;
 
@@ -80,7 +82,9 @@ int mp_convert(uint32_t *dst, mp_layout dst_layout, const uint32_t *src, mp_layo
  * Batch product C_k = A_k * B_k (Alg. 1 B_mul; Sec. 3 one-level Karatsuba).
  * a, b: n words per instance; c: 2n words per instance; all in `layout`.
  * algo: SCHOOLBOOK, KARATSUBA (one level, Sec. 3: three half-size products; sizes
- * above 512 bits, else MP_ERR_UNIMPLEMENTED) or AUTO (Karatsuba above 4096 bits).
+ * above 512 bits, else MP_ERR_UNIMPLEMENTED), KARATSUBA2 (two levels, the 9 quarter
+ * products of Sec. 3 applied twice; 4097..4608-bit and 3073..4096-bit sizes only, else
+ * MP_ERR_UNIMPLEMENTED) or AUTO (Karatsuba above 4096 bits).
  * c must not overlap a or b.
  */
 int mp_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmpgpu.so")
 
 LAYOUT_INSTANCE_MAJOR, LAYOUT_INTERLEAVED = 0, 1
-ALGO_AUTO, ALGO_SCHOOLBOOK, ALGO_KARATSUBA = 0, 1, 2
+ALGO_AUTO, ALGO_SCHOOLBOOK, ALGO_KARATSUBA, ALGO_KARATSUBA2 = 0, 1, 2, 3
 RED_TRUNCATED, RED_FULL, RED_CIOS = 0, 1, 2
 
 if not os.path.exists(LIB_PATH):

@@ -20,6 +20,8 @@ ShapeOps shape_ops_8_16();
 ShapeOps shape_ops_16_8();
 ShapeOps shape_ops_8_18();
 ShapeOps shape_ops_8_8_w();
+cudaError_t kara2_128(const KArgs &, cudaStream_t);
+cudaError_t kara2_144(const KArgs &, cudaStream_t);
 }  // namespace mpg
 
 using namespace mpg;
@@ -40,6 +42,7 @@ struct SizeClass {
     int chosen;          // index into shapes
     uint32_t window;     // default window for modexp (0: built-in rule)
     uint32_t kara_from;  // AUTO products use Karatsuba from this many bits (0: built-in rule)
+    cudaError_t (*kara2)(const KArgs &, cudaStream_t);   // two-level Karatsuba products, or null
 };
 static SizeClass g_classes[7];
 static bool g_classes_ready = false;
@@ -51,8 +54,8 @@ static void init_classes() {
     g_classes[2] = SizeClass{32, 2, {shape_ops_4_8(), shape_ops_8_4()}, 0, 0, 0};
     g_classes[3] = SizeClass{64, 3, {shape_ops_8_8(), shape_ops_16_4(), shape_ops_8_8_w()}, 0, 0, 0};
     g_classes[4] = SizeClass{96, 2, {shape_ops_8_12(), shape_ops_16_6()}, 0, 0, 0};
-    g_classes[5] = SizeClass{128, 2, {shape_ops_16_8(), shape_ops_8_16()}, 0, 0, 0};   // 16x8 measured faster
-    g_classes[6] = SizeClass{144, 1, {shape_ops_8_18()}, 0, 0, 0};
+    g_classes[5] = SizeClass{128, 2, {shape_ops_16_8(), shape_ops_8_16()}, 0, 0, 0, kara2_128};   // 16x8 faster
+    g_classes[6] = SizeClass{144, 1, {shape_ops_8_18()}, 0, 0, 0, kara2_144};
     g_classes_ready = true;
 }
 
@@ -158,7 +161,9 @@ extern "C" int mp_convert(uint32_t *dst, mp_layout dst_layout, const uint32_t *s
 static int check_common(size_t batch, uint32_t bits, mp_layout layout, mp_algo algo) {
     if (batch == 0) return MP_ERR_ARG;
     if (check_layout(layout)) return MP_ERR_ARG;
-    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
+        algo != MP_ALGO_KARATSUBA2)
+        return MP_ERR_ARG;
     if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
     return MP_OK;
 }
@@ -177,6 +182,8 @@ static int product(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t bat
     A.out = c; A.a = a; A.b = square ? a : b;
     A.batch = batch; A.cbatch = batch; A.n = (int)n; A.layout = (int)layout; A.square = square ? 1 : 0;
     const SizeClass *cls = class_for(n);
+    if (algo == MP_ALGO_KARATSUBA2)
+        return cls->kara2 ? cuda_status(cls->kara2(A, S(stream))) : MP_ERR_UNIMPLEMENTED;
     const uint32_t kfrom = cls->kara_from ? cls->kara_from : KARATSUBA_FROM_BITS;
     bool kara = algo == MP_ALGO_KARATSUBA || (algo == MP_ALGO_AUTO && bits >= kfrom);
     const ShapeOps *ksh = sh->kara ? sh : nullptr;   // any shape of the class with a Karatsuba kernel
@@ -379,8 +386,10 @@ static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, cons
                        mp_algo algo, bool square, void *stream) {
     if (!out || !a || (!square && !b) || !c) return MP_ERR_ARG;
     if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
-    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
-    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
+        algo != MP_ALGO_KARATSUBA2)
+        return MP_ERR_ARG;
+    if (algo == MP_ALGO_KARATSUBA || algo == MP_ALGO_KARATSUBA2) return MP_ERR_UNIMPLEMENTED;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(out) || !aligned16(a) || (!square && !aligned16(b))))
         return MP_ERR_ALIGN;
     KArgs A{};
@@ -462,8 +471,10 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
                                 size_t workspace_bytes, void *stream) {
     if (!y || !base || !c || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
     if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
-    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
-    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
+        algo != MP_ALGO_KARATSUBA2)
+        return MP_ERR_ARG;
+    if (algo == MP_ALGO_KARATSUBA || algo == MP_ALGO_KARATSUBA2) return MP_ERR_UNIMPLEMENTED;
     if (window == 0) window = tuned_window(c->bits);
     if (window > 6) return MP_ERR_SIZE;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp))))
@@ -570,8 +581,10 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
                                         void *stream) {
     if (!y || !base || !c || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
     if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
-    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA) return MP_ERR_ARG;
-    if (algo == MP_ALGO_KARATSUBA) return MP_ERR_UNIMPLEMENTED;
+    if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
+        algo != MP_ALGO_KARATSUBA2)
+        return MP_ERR_ARG;
+    if (algo == MP_ALGO_KARATSUBA || algo == MP_ALGO_KARATSUBA2) return MP_ERR_UNIMPLEMENTED;
     if (window == 0) window = tuned_window(c->bits);
     if (window > 6) return MP_ERR_SIZE;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp))))

@@ -132,6 +132,132 @@ __global__ void __launch_bounds__(TPB) k_kara(KArgs A) {
     gstore<2 * F::M>(A.out, x, A.layout, k, valid, 2 * g.t * F::M, 2 * A.n, A.batch);
 }
 
+// ------------------------------------------------------------------ two levels
+//
+// Two levels of Karatsuba (Sec. 3): the three half-size products of the level above are
+// themselves one-level Karatsuba products of quarter-size schoolbook blocks, 9 quarter
+// products instead of 16. One group shape QS (G threads, MQ words per thread) serves both
+// levels: QS::NP = q words per quarter, h = 2q per half, f = 4q per operand.
+
+// out[0 .. 4q) = x * y for x, y of 2q words (one Karatsuba level over quarter products).
+// Scratch: sx, sy (q words each), d1 (2q words + top), sq (2q words, block squares).
+template <class QS>
+MPG_DI void kara1(const Grp<QS> &g, const uint32_t *x, const uint32_t *y, bool square, uint32_t *out,
+                  uint32_t *sx, uint32_t *sy, uint32_t *d1, uint32_t *sq) {
+    constexpr int q = QS::NP, MQ = QS::M;
+    const uint32_t cx = gadd<QS, MQ>(g, sx, x, [&](int i) { return x[q + i]; }, 0u);
+    uint32_t cy = cx;
+    if (!square) cy = gadd<QS, MQ>(g, sy, y, [&](int i) { return y[q + i]; }, 0u);
+    const uint32_t *syp = square ? sx : sy;
+    if (square) {
+        phase_sqr<QS>(g, x, sq, out);
+        phase_sqr<QS>(g, x + q, sq, out + 2 * q);
+        phase_sqr<QS>(g, sx, sq, d1);
+    } else {
+        phase_mul<QS>(g, x, y, out);
+        phase_mul<QS>(g, x + q, y + q, out + 2 * q);
+        phase_mul<QS>(g, sx, sy, d1);
+    }
+    const uint32_t mx = 0u - cx, my = 0u - cy;
+    uint32_t top = gadd<QS, 2 * MQ>(g, d1, d1, [&](int i) { return i >= q ? (syp[i - q] & mx) : 0u; }, 0u);
+    top += gadd<QS, 2 * MQ>(g, d1, d1, [&](int i) { return i >= q ? (sx[i - q] & my) : 0u; }, 0u);
+    top += cx & cy;
+    top -= gsub<QS, 2 * MQ>(g, d1, d1, out);
+    top -= gsub<QS, 2 * MQ>(g, d1, d1, out + 2 * q);
+    gadd<QS, 4 * MQ>(g, out, out, [&](int i) {
+        return (i >= q && i < 3 * q) ? d1[i - q] : (i == 3 * q ? top : 0u);
+    }, 0u);
+}
+
+template <class QS>
+struct Kara2Layout {
+    static constexpr int q = QS::NP, h = 2 * q, f = 4 * q;
+    static constexpr int OFF_A = 0;                 // a (f)
+    static constexpr int OFF_B = f;                 // b (f)
+    static constexpr int OFF_SA = 2 * f;            // a_l + a_h (h)
+    static constexpr int OFF_SB = OFF_SA + h;       // b_l + b_h (h)
+    static constexpr int OFF_D = OFF_SB + h;        // D0 | D2 (2f): the result is formed in place
+    static constexpr int OFF_D1 = OFF_D + 2 * f;    // D1 (f words + top)
+    static constexpr int OFF_SX = OFF_D1 + f;       // inner level: s_x, s_y (q each)
+    static constexpr int OFF_SY = OFF_SX + q;
+    static constexpr int OFF_ID1 = OFF_SY + q;      // inner D1 (2q)
+    static constexpr int OFF_SQ = OFF_ID1 + 2 * q;  // inner block squares (2q)
+    static constexpr int OFF_P = OFF_SQ + 2 * q;    // slot spills of the quarter products
+    static constexpr int OFF_Z = OFF_P + 2 * QS::G * (QS::M + 2);
+    static constexpr int WORDS = (OFF_Z + QS::M + 3) & ~3;
+};
+
+template <class QS, int TPB>
+__global__ void __launch_bounds__(TPB) k_kara2(KArgs A) {
+    using L = Kara2Layout<QS>;
+    constexpr int q = L::q, h = L::h, G = QS::G, MQ = QS::M, MF = 4 * MQ;
+    extern __shared__ uint4 smem4[];
+    uint32_t *sm = reinterpret_cast<uint32_t *>(smem4) + (threadIdx.x / G) * L::WORDS;
+    Grp<QS> g;
+    g.sm = sm;
+    g.pa = sm + L::OFF_P;
+    g.za = sm + L::OFF_Z;
+    g.t = threadIdx.x % G;
+    g.gbase = (threadIdx.x & 31) & ~(G - 1);
+    const size_t k = (size_t)blockIdx.x * (TPB / G) + threadIdx.x / G;
+    const bool valid = k < A.batch;
+    uint32_t *a = sm + L::OFF_A, *b = sm + L::OFF_B, *sa = sm + L::OFF_SA, *sb = sm + L::OFF_SB;
+    uint32_t *D = sm + L::OFF_D, *D1 = sm + L::OFF_D1;
+    uint32_t *sx = sm + L::OFF_SX, *sy = sm + L::OFF_SY, *id1 = sm + L::OFF_ID1, *sq = sm + L::OFF_SQ;
+    if (g.t == 0) {
+#pragma unroll
+        for (int j = 0; j < MQ; ++j) g.za[j] = 0u;
+    }
+    {
+        uint32_t x[MF];
+        gload<MF>(x, A.a, A.layout, k, valid, g.t * MF, A.n, A.batch);
+        sts<MF>(a + g.t * MF, x);
+        if (!A.square) {
+            gload<MF>(x, A.b, A.layout, k, valid, g.t * MF, A.n, A.batch);
+            sts<MF>(b + g.t * MF, x);
+        }
+    }
+    g.sync();
+    const bool sqr = A.square != 0;
+    const uint32_t ca = gadd<QS, 2 * MQ>(g, sa, a, [&](int i) { return a[h + i]; }, 0u);
+    uint32_t cb = ca;
+    if (!sqr) cb = gadd<QS, 2 * MQ>(g, sb, b, [&](int i) { return b[h + i]; }, 0u);
+    const uint32_t *sbp = sqr ? sa : sb;
+    kara1<QS>(g, a, b, sqr, D, sx, sy, id1, sq);                 // D0 = a_l b_l
+    kara1<QS>(g, a + h, b + h, sqr, D + 2 * h, sx, sy, id1, sq); // D2 = a_h b_h
+    kara1<QS>(g, sa, sbp, sqr, D1, sx, sy, id1, sq);             // D1 = s_a s_b
+    const uint32_t ma = 0u - ca, mb = 0u - cb;
+    uint32_t top = gadd<QS, 4 * MQ>(g, D1, D1, [&](int i) { return i >= h ? (sbp[i - h] & ma) : 0u; }, 0u);
+    top += gadd<QS, 4 * MQ>(g, D1, D1, [&](int i) { return i >= h ? (sa[i - h] & mb) : 0u; }, 0u);
+    top += ca & cb;
+    top -= gsub<QS, 4 * MQ>(g, D1, D1, D);
+    top -= gsub<QS, 4 * MQ>(g, D1, D1, D + 2 * h);
+    // result = (D2 : D0) + W^h (D1 + W^2h top), in two halves of f words
+    const uint32_t c = gadd<QS, 4 * MQ>(g, D, D, [&](int i) { return i >= h ? D1[i - h] : 0u; }, 0u);
+    gadd<QS, 4 * MQ>(g, D + 2 * h, D + 2 * h, [&](int i) {
+        return i < h ? D1[h + i] : (i == h ? top : 0u);
+    }, c);
+    uint32_t x[2 * MF];
+    lds<2 * MF>(x, D + 2 * g.t * MF);
+    gstore<2 * MF>(A.out, x, A.layout, k, valid, 2 * g.t * MF, 2 * A.n, A.batch);
+}
+
+template <class QS, int TPB>
+static cudaError_t launch_kara2(const KArgs &A, cudaStream_t st) {
+    using L = Kara2Layout<QS>;
+    constexpr int GPB = TPB / QS::G;
+    const size_t smem = (size_t)GPB * L::WORDS * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_kara2<QS, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const size_t blocks = (A.batch + GPB - 1) / GPB;
+    k_kara2<QS, TPB><<<(unsigned)blocks, TPB, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
 template <class F, class HS, int TPB>
 static cudaError_t launch_kara(const KArgs &A, cudaStream_t st) {
     using L = KaraLayout<F, HS>;

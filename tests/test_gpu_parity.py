@@ -444,6 +444,36 @@ def test_warp_mapped_shape(mp, layout):
         mp.tune_set(bits, before["G"], before["M"], 0)
 
 
+@pytest.mark.parametrize("bits", [3100, 4000, 4096, 4108, 4154, 4608])
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_two_level_karatsuba(mp, bits, layout):
+    """Two levels of Karatsuba (9 quarter products) against the oracle, with operands that
+    make every half and quarter sum carry (all ones) next to random ones."""
+    batch = 45
+    b = si.make_batch(0, "test", batch, bits, ebits=1, sub=6000 + bits)
+    n = b.n
+    top = np.uint32((1 << (bits - 32 * (n - 1))) - 1) if bits % 32 else np.uint32(0xFFFFFFFF)
+    b.a[0, :] = 0xFFFFFFFF
+    b.a[0, -1] = top
+    b.b[0] = b.a[0]
+    b.a[1] = 0
+    A, B = dev(mp, b.a, layout), dev(mp, b.b, layout)
+    C = torch.zeros(mp.array_words(layout, batch, 2 * n), dtype=torch.int32, device="cuda")
+    mp.mp_mul(C, A, B, batch, bits, layout, mp.ALGO_KARATSUBA2)
+    assert_equal(host(mp, C, batch, 2 * n, layout), oracle.mul(b.a, b.b), f"karatsuba2 mul {bits}")
+    mp.mp_sqr(C, A, batch, bits, layout, mp.ALGO_KARATSUBA2)
+    assert_equal(host(mp, C, batch, 2 * n, layout), oracle.sqr(b.a), f"karatsuba2 sqr {bits}")
+
+
+def test_two_level_karatsuba_unavailable_sizes(mp):
+    b = si.make_batch(0, "test", 4, 2048, ebits=1, sub=77)
+    A = dev(mp, b.a, IL)
+    C = torch.zeros(mp.array_words(IL, 4, 2 * b.n), dtype=torch.int32, device="cuda")
+    with pytest.raises(mp.MpError) as e:
+        mp.mp_mul(C, A, A, 4, 2048, IL, mp.ALGO_KARATSUBA2)
+    assert e.value.status == -7
+
+
 # ------------------------------------------------------------------ resident tables, fixed bases
 
 @pytest.mark.parametrize("bits,window", [(1024, 4), (2048, 5), (3072, 5), (4096, 6)])
