@@ -255,7 +255,7 @@ int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *
  * from clock64) and the SM clock implied by the kernel's wall time.
  * mode 0: independent mad.lo.u32; 1: independent mad.hi.u32; 2: the library's 8x8
  * block product (mad.lo.cc/madc.hi.cc chains, counts its 128 multiply-adds);
- * 3: add.cc/addc.cc chains; 4: independent mad.wide.u32 (counted as 2); 5: 8x8 block
+ * 3: add.cc/addc.cc chains; 4: mad.wide.u32 chains fed by their own low word (counted as 2); 5: 8x8 block
  * product from mad.wide.u32 and 64-bit carry adds; 6: two independent 8x8 chain
  * products per iteration; 7: mode 2 on 256 threads per SM; 8: 10x10 block of 26-bit
  * digits summed into 64-bit columns by mad.wide.u32 (counted as 2 per product).

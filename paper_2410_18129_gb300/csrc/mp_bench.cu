@@ -13,7 +13,7 @@ using namespace mpg;
 // mode 1: independent high-half multiply-adds (mad.hi.u32)
 // mode 2: the library's 8x8 block product (mad.lo.cc / madc.hi.cc carry chains), 128 IMAD per call
 // mode 3: 32-bit add-with-carry chains (add.cc / addc.cc), 8 words
-// mode 4: independent mad.wide.u32 (32x32+64 -> 64), counted as two multiply-adds
+// mode 4: mad.wide.u32 (32x32+64 -> 64) chains fed by their own low word, counted as two multiply-adds
 // mode 5: 8x8 block product from mad.wide.u32 plus 64-bit carry adds
 // mode 6: two independent 8x8 carry-chain block products per iteration
 // mode 7: mode 2 with 256 active threads per SM
@@ -57,7 +57,8 @@ __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long
             }
         }
     } else if (mode == 4) {
-        // independent 32x32+64 -> 64 multiply-adds (mad.wide.u32), 8 chains; counted as 2 (lo + hi)
+        // 32x32+64 -> 64 multiply-adds (mad.wide.u32), 8 chains; counted as 2 (lo + hi). The
+        // multiplier is the chain's previous low word, so no product can be precomputed.
         uint64_t w[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) w[i] = ((uint64_t)a[i] << 32) | b[i];
@@ -66,7 +67,7 @@ __global__ void k_bench(int mode, int iters, uint32_t seed, uint32_t *sink, long
             for (int r = 0; r < 8; ++r) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[i]) : "r"(b[i]), "r"(a[(i + 1) & 7]));
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[i]) : "r"((uint32_t)w[i]), "r"(a[(i + 1) & 7]));
             }
         }
 #pragma unroll
