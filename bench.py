@@ -172,6 +172,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--quick", action="store_true",
                     help="time the modexp steps only (no comparison runs, no e2e, no CPU baseline): for profiling")
+    ap.add_argument("--reduction", default="truncated", choices=["truncated", "full", "cios"],
+                    help="reduction of the timed modexp steps with --quick (profiling); the full line "
+                         "always times the truncated one and reports the others beside it")
     ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096", "mixed", "serving"],
                     help="batch_2048: the headline line; batch_4096: 4096-bit products (schoolbook vs "
                          "Karatsuba, 4108/4154 edges), Montgomery and w=6 modexp")
@@ -241,7 +244,11 @@ def main():
         reps.barrier(info)
         torch.cuda.synchronize()
 
-    def step(red=mp.RED_TRUNCATED):
+    quick_red = {"truncated": mp.RED_TRUNCATED, "full": mp.RED_FULL, "cios": mp.RED_CIOS}[args.reduction]
+    if not args.quick and quick_red != mp.RED_TRUNCATED:
+        raise SystemExit("--reduction applies to --quick runs only")
+
+    def step(red=quick_red):
         mp.modexp_consttime(Y, A, E, ebits, ctx, WINDOW, red, workspace=ws)
 
     def timed(fn, k):
@@ -274,7 +281,7 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "modexp/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                              "quick": True, "batch_per_gpu": B, "clocks": clocks}))
+                              "quick": True, "reduction": args.reduction, "batch_per_gpu": B, "clocks": clocks}))
         ctx.free()
         return
 
