@@ -474,6 +474,43 @@ def test_two_level_karatsuba_unavailable_sizes(mp):
     assert e.value.status == -7
 
 
+BOUNDARY_SIZES = [2, 3, 31, 32, 33, 63, 65, 255, 256, 257, 511, 513, 1023, 1025, 2047, 2049,
+                  3071, 3073, 4095, 4097, 4607, 4608]
+
+
+@pytest.mark.parametrize("bits", BOUNDARY_SIZES)
+def test_size_class_boundaries(mp, bits):
+    """Every size-class edge (one word less / more than a padded size, the smallest and the
+    largest sizes): products, all three reductions, and a short exponentiation, on a ragged batch."""
+    batch = 33
+    b = si.make_batch(0, "test", batch, bits, ebits=min(bits, 96), sub=8000 + bits)
+    n = b.n
+    A, B = dev(mp, b.a, IL), dev(mp, b.b, IL)
+    C2 = torch.zeros(mp.array_words(IL, batch, 2 * n), dtype=torch.int32, device="cuda")
+    mp.mp_mul(C2, A, B, batch, bits, IL)
+    assert_equal(host(mp, C2, batch, 2 * n, IL), oracle.mul(b.a, b.b), f"mp_mul {bits}")
+    mp.mp_sqr(C2, A, batch, bits, IL)
+    assert_equal(host(mp, C2, batch, 2 * n, IL), oracle.sqr(b.a), f"mp_sqr {bits}")
+    ctx = mp.MontCtx(dev(mp, b.N, IL), batch, bits, IL)
+    C = out_tensor(mp, batch, n, IL)
+    want_mul, want_sqr = oracle.mont_def(b.a, b.b, b.N), oracle.mont_def(b.a, b.a, b.N)
+    want_exp = oracle.modexp(b.a, b.e, b.ebits, b.N)
+    for red in (0, 1, 2):
+        mp.mont_mul(C, A, B, ctx, red)
+        assert_equal(host(mp, C, batch, n, IL), want_mul, f"mont_mul {bits} red={red}")
+        mp.mont_sqr(C, A, ctx, red)
+        assert_equal(host(mp, C, batch, n, IL), want_sqr, f"mont_sqr {bits} red={red}")
+        mp.modexp_consttime(C, A, dev(mp, b.e, IL), b.ebits, ctx, 3, red)
+        assert_equal(host(mp, C, batch, n, IL), want_exp, f"modexp {bits} red={red}")
+    ctx.free()
+
+
+def test_bits_above_the_largest_class_are_rejected(mp):
+    b = si.make_batch(0, "test", 2, 4608, ebits=1, sub=4609)
+    with pytest.raises(mp.MpError):
+        mp.MontCtx(dev(mp, np.concatenate([b.N, np.ones((2, 1), np.uint32)], axis=1), IL), 2, 4609, IL)
+
+
 # ------------------------------------------------------------------ resident tables, fixed bases
 
 @pytest.mark.parametrize("bits,window", [(1024, 4), (2048, 5), (3072, 5), (4096, 6)])
