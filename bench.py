@@ -560,6 +560,10 @@ def bench_mixed(args):
     with ClockSampler(0) as clk:
         ms_mixed = timed(mixed, k)
     ms_graph = timed(graph.replay, k)
+    # the same persistent launch with the word-serial CIOS reduction (Alg. 4), for comparison
+    cios = lambda: mp.modexp_consttime_mixed(jobs, mp.RED_CIOS, ws)
+    cios()
+    ms_cios = timed(cios, k)
     # parity: each size class, sampled instances of the graph-replayed results vs the oracle
     torch.cuda.synchronize()
     mism, sampled = 0, 0
@@ -581,6 +585,7 @@ def bench_mixed(args):
                                + " bits, random odd moduli, full-length exponents, truncated Montgomery",
                    "tuned": {b: {k2: v for k2, v in c.items() if k2 != "timings"} for b, c in choice.items()}},
         "plain_per_size_launches_per_s": total / (ms_plain / 1e3),
+        "cios_persistent_per_s": total / (ms_cios / 1e3),
         "e2e": {"value": total / (ms_graph / 1e3), "unit": "modexp/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "form": "CUDA graph: H2D copies + persistent launch + D2H copies"},
         "gpu_launches": 1, "clocks": clk.summary(), "parity": {"sampled": sampled, "mismatches": mism},

@@ -166,7 +166,7 @@ int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uin
  * ONE kernel launch: blocks pull tiles of instances from an atomic counter, the
  * costliest job first, so the launch can be captured in a CUDA graph together with
  * its input copies. Results equal those of modexp_consttime on each job.
- * red: MP_RED_TRUNCATED or MP_RED_FULL (MP_RED_CIOS: MP_ERR_UNIMPLEMENTED).
+ * red: MP_RED_TRUNCATED, MP_RED_FULL or MP_RED_CIOS, for every job of the call.
  * workspace: at least modexp_mixed_workspace_bytes(jobs, njobs) bytes, 256-byte
  * aligned (window tables plus the tile counter, which the call resets on `stream`).
  */

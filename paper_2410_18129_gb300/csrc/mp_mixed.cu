@@ -1,88 +1,8 @@
-// Mixed-size constant-time exponentiation in one persistent launch.
-//
-// Instances of several sizes (each job = one Montgomery context and its bases,
-// exponents and outputs) are cut into tiles of one block's worth of instances.
-// Tiles are numbered job by job, the costliest job first, and every resident
-// block pulls the next tile number from one atomic counter until none are left,
-// so the large instances start first and the small ones fill the tail. A tile
-// runs the same per-group exponentiation as the one-size kernel, with the group
-// shape of its size class. Only sizes, shapes and tile numbers (public data)
-// decide the control flow.
-#include <cuda_runtime.h>
-#include <algorithm>
-#include "mp_internal.h"
+// Mixed-size constant-time exponentiation in one persistent launch: job checks,
+// workspace, tile numbering and the launch (the kernel is in mp_mixed.cuh).
+#include "mp_mixed.cuh"
 
 namespace mpg {
-
-constexpr int MIX_TPB = 256;
-constexpr int MIX_MAX_JOBS = 16;
-
-// every compiled group shape of the sizes up to 4096 bits; a job runs with the shape
-// currently selected for its size class (see mp_tune_set)
-using MixS0 = Shape<4, 4>;    //  512 bits
-using MixS1 = Shape<4, 8>;    // 1024 bits
-using MixS2 = Shape<8, 4>;    // 1024 bits
-using MixS3 = Shape<8, 8>;    // 2048 bits
-using MixS4 = Shape<16, 4>;   // 2048 bits
-using MixS5 = Shape<8, 12>;   // 3072 bits
-using MixS6 = Shape<16, 6>;   // 3072 bits
-using MixS7 = Shape<16, 8>;   // 4096 bits
-constexpr int MIX_NSHAPES = 8;
-
-template <class S>
-constexpr size_t mix_smem() { return (size_t)(MIX_TPB / S::G) * S::WORDS * 4; }
-constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t MIX_SMEM =
-    cmax(cmax(cmax(mix_smem<MixS0>(), mix_smem<MixS1>()), cmax(mix_smem<MixS2>(), mix_smem<MixS3>())),
-         cmax(cmax(mix_smem<MixS4>(), mix_smem<MixS5>()), cmax(mix_smem<MixS6>(), mix_smem<MixS7>())));
-
-struct MixJob {
-    KArgs A;
-    int shape;   // 0..7: MixS0..MixS7
-    int tile0;   // first tile number of this job
-};
-
-struct MixArgs {
-    MixJob job[MIX_MAX_JOBS];
-    int njobs;
-    int total;           // tiles over all jobs
-    unsigned *counter;   // next tile number (zeroed before the launch)
-};
-
-template <class S, int RED>
-MPG_DI void mix_tile(const KArgs &A, int tile, uint32_t *smem) {
-    Grp<S> g = make_group<S>(smem);
-    const size_t k = (size_t)tile * (MIX_TPB / S::G) + threadIdx.x / S::G;
-    modexp_group<S, RED>(g, A, k);
-}
-
-template <int RED>
-__global__ void __launch_bounds__(MIX_TPB, 2) k_modexp_mixed(const __grid_constant__ MixArgs P) {
-    extern __shared__ uint4 smem4[];
-    uint32_t *smem = reinterpret_cast<uint32_t *>(smem4);
-    __shared__ int s_tile;
-    for (;;) {
-        __syncthreads();   // the previous tile is finished in every warp
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(P.counter, 1u);
-        __syncthreads();
-        const int tile = s_tile;
-        if (tile >= P.total) break;
-        int j = 0;
-        while (j + 1 < P.njobs && tile >= P.job[j + 1].tile0) ++j;
-        const MixJob &J = P.job[j];
-        const int local = tile - J.tile0;
-        switch (J.shape) {
-            case 0: mix_tile<MixS0, RED>(J.A, local, smem); break;
-            case 1: mix_tile<MixS1, RED>(J.A, local, smem); break;
-            case 2: mix_tile<MixS2, RED>(J.A, local, smem); break;
-            case 3: mix_tile<MixS3, RED>(J.A, local, smem); break;
-            case 4: mix_tile<MixS4, RED>(J.A, local, smem); break;
-            case 5: mix_tile<MixS5, RED>(J.A, local, smem); break;
-            case 6: mix_tile<MixS6, RED>(J.A, local, smem); break;
-            default: mix_tile<MixS7, RED>(J.A, local, smem); break;
-        }
-    }
-}
 
 // the persistent kernel's shape id for this context: the shape selected for its size
 // class if the kernel has it, else another compiled shape of the same padded size
@@ -112,26 +32,6 @@ static size_t job_table_bytes(const mp_modexp_job &j) {
 }
 
 static size_t job_instances(const mp_modexp_job &j) { return j.index ? j.nreq : j.ctx->batch; }
-
-template <int RED>
-static cudaError_t launch_mixed(const MixArgs &P, cudaStream_t st) {
-    static int grid = 0;   // resident blocks over the whole GPU, computed once per process
-    if (!grid) {
-        cudaError_t e = cudaFuncSetAttribute(k_modexp_mixed<RED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)MIX_SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_modexp_mixed<RED>, MIX_TPB, MIX_SMEM)) !=
-            cudaSuccess)
-            return e;
-        grid = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    const int blocks = std::min(grid, P.total > 0 ? P.total : 1);
-    k_modexp_mixed<RED><<<blocks, MIX_TPB, MIX_SMEM, st>>>(P);
-    return cudaGetLastError();
-}
 
 }  // namespace mpg
 
@@ -166,8 +66,7 @@ extern "C" int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_r
                                       size_t workspace_bytes, void *stream) {
     int rc = check_jobs(jobs, njobs);
     if (rc != MP_OK) return rc;
-    if (red == MP_RED_CIOS) return MP_ERR_UNIMPLEMENTED;   // the persistent kernel carries Alg. 5/6 only
-    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
     if (!workspace || ((uintptr_t)workspace & 255u)) return workspace ? MP_ERR_ALIGN : MP_ERR_ARG;
     if (workspace_bytes < modexp_mixed_workspace_bytes(jobs, njobs)) return MP_ERR_NOMEM;
     // costliest job first: cost per instance ~ words^2 * exponent bits
@@ -213,6 +112,8 @@ extern "C" int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_r
     P.total = tile;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(P.counter, 0, sizeof(unsigned), st) != cudaSuccess) return MP_ERR_CUDA;
-    const cudaError_t e = red == MP_RED_TRUNCATED ? launch_mixed<0>(P, st) : launch_mixed<1>(P, st);
+    const cudaError_t e = red == MP_RED_TRUNCATED ? launch_mixed_red0(P, st)
+                          : red == MP_RED_FULL    ? launch_mixed_red1(P, st)
+                                                  : launch_mixed_red2(P, st);
     return e == cudaSuccess ? MP_OK : MP_ERR_CUDA;
 }
