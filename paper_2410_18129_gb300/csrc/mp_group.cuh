@@ -189,6 +189,40 @@ MPG_DI void mac_block(uint32_t (&V)[2 * B + 2], const uint32_t *xp, const uint32
     acc_add<B>(V, P);
 }
 
+// V += X_{u(j)} * Y_{v(j)} for j = 0 .. cnt-1 (B-word blocks; uv(j, u, v) gives the pair), with
+// the operands of step j+1 loaded from shared memory while step j multiplies (two register
+// buffers, the loop unrolled by two so they alternate without moves). at(j) runs after step j.
+template <int B, class UV, class AT>
+MPG_DI void mac_loop_pipelined(uint32_t (&V)[2 * B + 2], const uint32_t *X, const uint32_t *Y, int cnt,
+                               const UV &uv, const AT &at) {
+    uint32_t xa[B], ya[B], xb[B], yb[B], P[2 * B];
+    int u, v;
+    uv(0, u, v);
+    lds<B>(xa, X + u * B);
+    lds<B>(ya, Y + v * B);
+    int j = 0;
+    MPG_BLOCK_LOOP
+    for (; j + 1 < cnt; j += 2) {
+        uv(j + 1, u, v);
+        lds<B>(xb, X + u * B);
+        lds<B>(yb, Y + v * B);
+        block_mul<B>(P, xa, ya);
+        acc_add<B>(V, P);
+        at(j);
+        uv(j + 2 < cnt ? j + 2 : j + 1, u, v);   // the last pair reloads in-range operands
+        lds<B>(xa, X + u * B);
+        lds<B>(ya, Y + v * B);
+        block_mul<B>(P, xb, yb);
+        acc_add<B>(V, P);
+        at(j + 1);
+    }
+    if (j < cnt) {
+        block_mul<B>(P, xa, ya);
+        acc_add<B>(V, P);
+        at(j);
+    }
+}
+
 // ------------------------------------------------------------------ carry resolution
 
 enum SlotPattern { PAT_SEQ = 0, PAT_ZIGZAG = 1, PAT_ONE = 2 };
@@ -508,14 +542,13 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
         MPG_BLOCK_LOOP
         for (int j = t + 1; j <= 2 * G; ++j) mac_block<H>(V, X + (j - t - 1) * H, Y + (2 * G - j) * H);
     } else {
-        MPG_BLOCK_LOOP
-        for (int j = 0; j <= 2 * G; ++j) {
-            int u, v;
-            if (j <= t) { u = j; v = t - j; }
-            else { u = j - t - 1; v = 2 * G - j; }
-            mac_block<H>(V, X + u * H, Y + v * H);
-            if (j == t) park<H>(V, Q + t * H, g.P() + t * (H + 2));
-        }
+        mac_loop_pipelined<H>(
+            V, X, Y, 2 * G + 1,
+            [&](int j, int &u, int &v) {
+                if (j <= t) { u = j; v = t - j; }
+                else { u = j - t - 1; v = 2 * G - j; }
+            },
+            [&](int j) { if (j == t) park<H>(V, Q + t * H, g.P() + t * (H + 2)); });
         unpark_sub<H>(V, Q + t * H, g.P() + t * (H + 2));
     }
     park<H>(V, Q + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
@@ -625,14 +658,13 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
         MPG_BLOCK_LOOP
         for (int j = nA; j < 2 * G - 1; ++j) mac_block<H>(V, Qs + (j + 1) * H, Ns + (4 * G - 2 - t - j) * H);
     } else {
-        MPG_BLOCK_LOOP
-        for (int j = 0; j < 2 * G - 1; ++j) {
-            int u, v;
-            if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
-            else { u = j + 1; v = 4 * G - 2 - t - j; }
-            mac_block<H>(V, Qs + u * H, Ns + v * H);
-            if (j == nA - 1) park<H>(V, C + t * H, g.P() + t * (H + 2));
-        }
+        mac_loop_pipelined<H>(
+            V, Qs, Ns, 2 * G - 1,
+            [&](int j, int &u, int &v) {
+                if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
+                else { u = j + 1; v = 4 * G - 2 - t - j; }
+            },
+            [&](int j) { if (j == nA - 1) park<H>(V, C + t * H, g.P() + t * (H + 2)); });
         unpark_sub<H>(V, C + t * H, g.P() + t * (H + 2));
     }
     park<H>(V, C + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
