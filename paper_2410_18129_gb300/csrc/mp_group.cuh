@@ -536,11 +536,11 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
     zero<A>(V);
     const int t = g.t;
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
-        MPG_BLOCK_LOOP
-        for (int j = 0; j <= t; ++j) mac_block<H>(V, X + j * H, Y + (t - j) * H);
+        const auto none = [](int) {};
+        mac_loop_pipelined<H>(V, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; }, none);
         flush<H>(V, Q + t * H, g.P() + t * (H + 2));
-        MPG_BLOCK_LOOP
-        for (int j = t + 1; j <= 2 * G; ++j) mac_block<H>(V, X + (j - t - 1) * H, Y + (2 * G - j) * H);
+        mac_loop_pipelined<H>(V, X, Y, 2 * G - t, [&](int k, int &u, int &v) { u = k; v = 2 * G - t - 1 - k; },
+                              none);
     } else {
         mac_loop_pipelined<H>(
             V, X, Y, 2 * G + 1,
@@ -649,14 +649,13 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
     const int t = g.t;
     const int nA = 2 * G - 1 - t;
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
-        MPG_BLOCK_LOOP
-        for (int j = 0; j < nA; ++j) {
-            const int u = t + 1 + j;
-            mac_block<H>(V, Qs + u * H, Ns + (2 * G + t - u) * H);
-        }
+        const auto none = [](int) {};
+        mac_loop_pipelined<H>(V, Qs, Ns, nA, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; },
+                              none);
         flush<H>(V, C + t * H, g.P() + t * (H + 2));
-        MPG_BLOCK_LOOP
-        for (int j = nA; j < 2 * G - 1; ++j) mac_block<H>(V, Qs + (j + 1) * H, Ns + (4 * G - 2 - t - j) * H);
+        if (t > 0)   // slot B of thread t has t products (none for thread 0)
+            mac_loop_pipelined<H>(V, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; },
+                                  none);
     } else {
         mac_loop_pipelined<H>(
             V, Qs, Ns, 2 * G - 1,
