@@ -61,9 +61,16 @@ struct Shape {
     static constexpr int OFF_XB = OFF_Z + M;      // W_: one byte per thread (predicate exchange)
     static constexpr int OFF_XW = OFF_XB + (W_ ? (G + 3) / 4 : 0);   // W_: one broadcast word
     static constexpr int WORDS_RAW = OFF_XW + (W_ ? 1 : 0);
-    // keep every instance 16-byte aligned; with W_, 32 lanes read the same offset of 32
-    // instances: a stride of 4 (mod 8) words puts 8 lanes' 16-byte loads on distinct banks
-    static constexpr int WORDS = W_ ? ((WORDS_RAW + 3) / 8) * 8 + 4 : (WORDS_RAW + 3) & ~3;
+    // Instance stride (words), a multiple of 4 (16-byte aligned instances).
+    // Lane mapping: a half-warp's 8-byte accesses (spill words, carries) touch 16/G instances
+    // at the same offsets; a stride of 2G (mod 32) words spreads them evenly over the 32 banks
+    // (G = 16: one instance per half-warp; 16 (mod 32) separates the two of a warp).
+    // Warp mapping: 32 lanes read the same offset of 32 instances; a stride of 4 (mod 8)
+    // words puts 8 lanes' 16-byte loads on distinct banks.
+    static constexpr int BANK_RES = G < 16 ? 2 * G : 16;
+    static constexpr int WORDS_A = (WORDS_RAW + 3) & ~3;
+    static constexpr int WORDS = W_ ? ((WORDS_RAW + 3) / 8) * 8 + 4
+                                    : WORDS_A + ((BANK_RES - WORDS_A % 32) % 32 + 32) % 32;
 };
 
 // Per-thread view of its group.
@@ -222,6 +229,11 @@ MPG_DI void mac_loop_pipelined(uint32_t (&V)[2 * B + 2], const uint32_t *X, cons
         at(j);
     }
 }
+
+// The double-buffered loop pays for 4-word half blocks (measured); with wider half blocks
+// the extra registers cost more than the hidden load latency.
+template <class S>
+constexpr bool PIPELINE_HALF_BLOCKS = (S::H <= 4);
 
 // ------------------------------------------------------------------ carry resolution
 
@@ -542,13 +554,22 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
         mac_loop_pipelined<H>(V, X, Y, 2 * G - t, [&](int k, int &u, int &v) { u = k; v = 2 * G - t - 1 - k; },
                               none);
     } else {
-        mac_loop_pipelined<H>(
-            V, X, Y, 2 * G + 1,
-            [&](int j, int &u, int &v) {
-                if (j <= t) { u = j; v = t - j; }
-                else { u = j - t - 1; v = 2 * G - j; }
-            },
-            [&](int j) { if (j == t) park<H>(V, Q + t * H, g.P() + t * (H + 2)); });
+        const auto uv = [&](int j, int &u, int &v) {
+            if (j <= t) { u = j; v = t - j; }
+            else { u = j - t - 1; v = 2 * G - j; }
+        };
+        const auto at = [&](int j) { if (j == t) park<H>(V, Q + t * H, g.P() + t * (H + 2)); };
+        if constexpr (PIPELINE_HALF_BLOCKS<S>) {
+            mac_loop_pipelined<H>(V, X, Y, 2 * G + 1, uv, at);
+        } else {
+            MPG_BLOCK_LOOP
+            for (int j = 0; j <= 2 * G; ++j) {
+                int u, v;
+                uv(j, u, v);
+                mac_block<H>(V, X + u * H, Y + v * H);
+                at(j);
+            }
+        }
         unpark_sub<H>(V, Q + t * H, g.P() + t * (H + 2));
     }
     park<H>(V, Q + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
@@ -657,13 +678,22 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
             mac_loop_pipelined<H>(V, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; },
                                   none);
     } else {
-        mac_loop_pipelined<H>(
-            V, Qs, Ns, 2 * G - 1,
-            [&](int j, int &u, int &v) {
-                if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
-                else { u = j + 1; v = 4 * G - 2 - t - j; }
-            },
-            [&](int j) { if (j == nA - 1) park<H>(V, C + t * H, g.P() + t * (H + 2)); });
+        const auto uv = [&](int j, int &u, int &v) {
+            if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
+            else { u = j + 1; v = 4 * G - 2 - t - j; }
+        };
+        const auto at = [&](int j) { if (j == nA - 1) park<H>(V, C + t * H, g.P() + t * (H + 2)); };
+        if constexpr (PIPELINE_HALF_BLOCKS<S>) {
+            mac_loop_pipelined<H>(V, Qs, Ns, 2 * G - 1, uv, at);
+        } else {
+            MPG_BLOCK_LOOP
+            for (int j = 0; j < 2 * G - 1; ++j) {
+                int u, v;
+                uv(j, u, v);
+                mac_block<H>(V, Qs + u * H, Ns + v * H);
+                at(j);
+            }
+        }
         unpark_sub<H>(V, C + t * H, g.P() + t * (H + 2));
     }
     park<H>(V, C + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
