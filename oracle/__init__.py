@@ -11,8 +11,10 @@ Functions and the passages they follow:
 * ``ctx(N)``                      N' = (-N)^{-1} mod R, R mod N, R^2 mod N with R = 2^(32n) (Sec. 4)
 * ``mont_def(a, b, N)``           a*b*R^{-1} mod N, canonical (Alg. 3/5 "Ensure", canonical reading)
 * ``modexp(a, e, ebits, N)``      a^e mod N by left-to-right square-and-multiply (Alg. 7 "Ensure")
-* ``mont_model(a, b, N, red)``    the paper's reductions: red=0 truncated (Alg. 6), 1 classical (Alg. 5)
+* ``mont_model(a, b, N, red)``    the paper's reductions: red=0 truncated (Alg. 6), 1 classical (Alg. 5),
+                                  3 truncated with the Karatsuba high half (Sec. 5.1; n even)
 * ``montred_alg6(T, N, Np)``      one truncated reduction with its intermediates (Thm. 1, Thm. 2)
+* ``montred_tkara(T, N, Np)``     the same in the truncated Karatsuba form (Sec. 5.1)
 * ``modexp_alg7(a, e, ebits, N, w, red)``  fixed-window exponentiation (Alg. 7)
 """
 from __future__ import annotations
@@ -44,6 +46,7 @@ def _load():
             "or_batch_modexp_alg7": [P, P, P, I, P, L, I, I, I, I],
             "or_montred_alg6": [P, P, P, P, P, I, P, ctypes.POINTER(ctypes.c_long)],
             "or_montred_alg5": [P, P, P, P, P, I],
+            "or_montred_tkara": [P, P, P, P, P, I, P, ctypes.POINTER(ctypes.c_long)],
             "or_threads_used": [I],
             "or_mod": [P, P, I, P, I],
         }
@@ -153,6 +156,24 @@ def montred_alg6(T, N, Np):
     return {"C": C, "Cpre": Cpre, "c_add": int(dbg[0]),
             "S": int(dbg[1]) | (int(dbg[2]) << 32), "kappa": int(dbg[3]),
             "H": dbg[4:4 + n + 1].copy(), "pp": int(pp.value)}
+
+
+def montred_tkara(T, N, Np):
+    """One truncated reduction in the Karatsuba form (Sec. 5.1) of a single T (2n words,
+    n even). Returns a dict with C (canonical), Cpre (n+1 words), c_add, e (the signed
+    error of the column-(n-1) estimate), H (n+1 words) and pp."""
+    T, N, Np = _c(T).ravel(), _c(N).ravel(), _c(Np).ravel()
+    n = N.size
+    C = np.zeros(n, np.uint32)
+    Cpre = np.zeros(n + 1, np.uint32)
+    dbg = np.zeros(n + 3, np.uint32)
+    pp = ctypes.c_long(0)
+    rc = _load().or_montred_tkara(_p(C), _p(Cpre), _p(T), _p(N), _p(Np), n, _p(dbg), ctypes.byref(pp))
+    if rc:
+        raise ValueError("odd n" if rc == -1 else "estimate outside the recoverable range")
+    e = int(dbg[1])
+    return {"C": C, "Cpre": Cpre, "c_add": int(dbg[0]), "e": e - (1 << 32) if e >= 1 << 31 else e,
+            "H": dbg[2:2 + n + 1].copy(), "pp": int(pp.value)}
 
 
 def montred_alg5(T, N, Np):

@@ -18,6 +18,8 @@
  *   method model (the paper's steps, used to pin intermediates)
  *     or_montred_alg5 classical reduction q = T*N' mod R, C = (T+qN)/R        (Alg. 3 / Alg. 5)
  *     or_montred_alg6 truncated reduction: c_add, column n-1 sum, high half   (Alg. 6, Thm. 1, Thm. 2)
+ *     or_montred_tkara truncated reduction, Karatsuba form: D2 in full, column
+ *                     estimates of D0 and D1, carry from word n-1 of -T    (Sec. 5.1, Karatsuba)
  *     or_modexp_alg7  fixed-window left-to-right exponentiation               (Alg. 7)
  *
  * Reading adopted where the paper is silent: every Montgomery result is made
@@ -370,18 +372,175 @@ void or_montred_alg6(limb *C, limb *Cpre, const limb *T, const limb *N, const li
     free(H);
 }
 
-/* Montgomery product through one of the two reductions: red 0 = Alg. 6, 1 = Alg. 5. */
+/* sub_at: a[pos ..] -= b[0 .. nb) modulo W^len (two's complement wrap) */
+static void sub_at(limb *a, int len, int pos, const limb *b, int nb) {
+    dlimb borrow = 0;
+    for (int i = pos; i < len; ++i) {
+        dlimb d = (dlimb)a[i] - (i - pos < nb ? b[i - pos] : 0u) - borrow;
+        a[i] = (limb)d;
+        borrow = (d >> 32) & 1u;
+    }
+}
+
+/* P = (x*y) mod W^h for x, y of h words: lo halves of the pairs with i+j < h, hi halves
+   of the pairs with i+j+1 < h (h^2 half products) */
+static void low_half(limb *P, const limb *x, const limb *y, int h, long *pp) {
+    memset(P, 0, sizeof(limb) * (size_t)h);
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; i + j < h; ++j) {
+            dlimb p = (dlimb)x[i] * y[j];
+            add_at(P, h, i + j, (limb)p);
+            ++*pp;
+            if (i + j + 1 < h) { add_at(P, h, i + j + 1, p >> 32); ++*pp; }
+        }
+}
+
+/* x + y over h words (carry returned) */
+static limb half_sum(limb *s, const limb *x, const limb *y, int h) {
+    memcpy(s, x, sizeof(limb) * (size_t)h);
+    return add_n(s, y, h);
+}
+
+/*
+ * Column estimate of floor(x*y / W^(h-1)) for x, y of h words (the truncated half
+ * product of Sec. 5.1, computed like Eq. qnhat one word lower): lo halves of the
+ * pairs with i+j >= h-1 at word i+j-(h-1), hi halves of the pairs with i+j >= h-2 at
+ * word i+j+1-(h-1). U (h+2 words). The omitted partial products all sit below column
+ * h-1 and carry less than 2h into it, so U <= floor(xy / W^(h-1)) < U + 2h.
+ */
+static void trunc_est(limb *U, const limb *x, const limb *y, int h, long *pp) {
+    memset(U, 0, sizeof(limb) * (size_t)(h + 2));
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < h; ++j) {
+            int k = i + j;
+            dlimb p = (dlimb)x[i] * y[j];
+            if (k >= h - 1) { add_at(U, h + 2, k - (h - 1), (limb)p); ++*pp; }
+            if (k >= h - 2) { add_at(U, h + 2, k + 2 - h, p >> 32); ++*pp; }
+        }
+}
+
+/*
+ * Truncated Montgomery reduction with one level of Karatsuba (Sec. 5.1, the
+ * Karatsuba paragraph), n = 2h words, X_l / X_h the low / high h words of X:
+ *   q = (T mod R) N' mod R from the low half of a Karatsuba product only:
+ *       D0' = T_l N'_l in full; of D1' = (T_l + T_h)(N'_l + N'_h) and D2' = T_h N'_h
+ *       only the low h words:  q_l = D0'_l,  q_h = D0'_h + D1'_l - D0'_l - D2'_l  (mod W^h)
+ *   qN = W^2h D2 + W^h (D1 - D0 - D2) + D0,  D0 = q_l N_l, D2 = q_h N_h,
+ *       D1 = (q_l + q_h)(N_l + N_h) = s_q s_N + W^h (c_q s_N + c_N s_q) + W^2h c_q c_N
+ *   floor(qN / R) ~ D2_l + D1_h - D0_h - D2_h + W^h D2_h   (the paper's truncated form)
+ * Only D2 is formed in full; D0 and s_q s_N enter through their column estimates
+ * U0, U1 (trunc_est), one word below the half boundary, so that the sum
+ *   S = W D2 + U1 + W (c_q s_N + c_N s_q) + W^(h+1) c_q c_N - U0 - floor(D2 / W^(h-1))
+ *       + floor(U0 / W^h)
+ * estimates floor(qN / W^(n-1)) to within a few units. Word n-1 of qN is known
+ * (L = (-T) mod R, Thm. 1), so the error is e = (L[n-1] - S) mod W read as a signed
+ * word, and floor(qN / R) = floor((S + e) / W) exactly (the "carry evaluation" the
+ * paper carries over from the schoolbook case).
+ *   Cpre = floor(T / R) + floor(qN / R) + c_add.
+ * dbg (optional, n+3 words): [c_add, e, H[0..n]]; pp_count: 32x32-bit half products
+ * (lo or hi) of the reduction. Returns -1 for odd n, -2 if the recovered value is
+ * inconsistent (an estimate outside the recoverable range).
+ */
+int or_montred_tkara(limb *C, limb *Cpre, const limb *T, const limb *N, const limb *Np, int n,
+                     limb *dbg, long *pp_count) {
+    if (n < 2 || (n & 1)) return -1;
+    const int h = n / 2;
+    long pp = 0;
+    limb *buf = (limb *)calloc((size_t)(24 * h + 16), sizeof(limb));
+    limb *D0p = buf;                 /* 2h */
+    limb *sT = D0p + 2 * h;          /* h  */
+    limb *sNp = sT + h;              /* h  */
+    limb *P = sNp + h;               /* 2h scratch product */
+    limb *q = P + 2 * h;             /* 2h */
+    limb *sq = q + 2 * h;            /* h  */
+    limb *sN = sq + h;               /* h  */
+    limb *D2 = sN + h;               /* 2h */
+    limb *U0 = D2 + 2 * h;           /* h+2 */
+    limb *U1 = U0 + h + 2;           /* h+2 */
+    limb *S = U1 + h + 2;            /* 2h+2 */
+    limb *L = S + 2 * h + 2;         /* n  */
+
+    /* q, low half of a Karatsuba product */
+    or_mul(D0p, T, h, Np, h);
+    pp += 2L * h * h;
+    half_sum(sT, T, T + h, h);
+    half_sum(sNp, Np, Np + h, h);
+    memcpy(q, D0p, sizeof(limb) * (size_t)(2 * h));
+    low_half(P, sT, sNp, h, &pp);       /* D1'_l */
+    add_n(q + h, P, h);
+    low_half(P, T + h, Np + h, h, &pp); /* D2'_l */
+    sub_n(q + h, P, h);
+    sub_n(q + h, D0p, h);
+
+    limb c_add = 0;
+    for (int i = 0; i < n; ++i) c_add |= T[i];
+    c_add = c_add ? 1u : 0u;
+    dlimb c = 1;                        /* L = (~T_lo + 1) mod R */
+    for (int i = 0; i < n; ++i) {
+        c += (dlimb)(limb)~T[i];
+        L[i] = (limb)c;
+        c >>= 32;
+    }
+
+    /* high half of qN */
+    const limb c_q = half_sum(sq, q, q + h, h);
+    const limb c_N = half_sum(sN, N, N + h, h);
+    or_mul(D2, q + h, h, N + h, h);
+    pp += 2L * h * h;
+    trunc_est(U0, q, N, h, &pp);
+    trunc_est(U1, sq, sN, h, &pp);
+
+    memset(S, 0, sizeof(limb) * (size_t)(2 * h + 2));
+    memcpy(S + 1, D2, sizeof(limb) * (size_t)(2 * h));               /* W D2 */
+    for (int i = 0; i < h + 2; ++i) add_at(S, 2 * h + 2, i, U1[i]);  /* U1 */
+    for (int i = 0; i < h; ++i) {                                    /* W (c_q s_N + c_N s_q) */
+        if (c_q) add_at(S, 2 * h + 2, 1 + i, sN[i]);
+        if (c_N) add_at(S, 2 * h + 2, 1 + i, sq[i]);
+    }
+    add_at(S, 2 * h + 2, h + 1, (dlimb)(c_q & c_N));                 /* W^(h+1) c_q c_N */
+    sub_at(S, 2 * h + 2, 0, U0, h + 2);                              /* - U0 */
+    sub_at(S, 2 * h + 2, 0, D2 + h - 1, h + 1);                      /* - floor(D2 / W^(h-1)) */
+    add_at(S, 2 * h + 2, 0, U0[h]);                                  /* + floor(U0 / W^h) */
+    const int32_t e = (int32_t)(L[n - 1] - S[0]);
+    if (e >= 0) {
+        add_at(S, 2 * h + 2, 0, (dlimb)e);
+    } else {
+        limb m = (limb)(-(int64_t)e);
+        sub_at(S, 2 * h + 2, 0, &m, 1);
+    }
+    int bad = (S[0] != L[n - 1]) || S[2 * h + 1] != 0;   /* S + e must be floor(qN / W^(n-1)) >= 0 */
+
+    /* Cpre = T_hi + H + c_add, H = S[1 .. n] */
+    memset(Cpre, 0, sizeof(limb) * (size_t)(n + 1));
+    memcpy(Cpre, S + 1, sizeof(limb) * (size_t)n);
+    Cpre[n] = add_n(Cpre, T + n, n);
+    add_at(Cpre, n + 1, 0, c_add);
+    final_subtract(C, Cpre, N, n);
+    if (dbg) {
+        dbg[0] = c_add;
+        dbg[1] = (limb)e;
+        memcpy(dbg + 2, S + 1, sizeof(limb) * (size_t)(n + 1));
+    }
+    if (pp_count) *pp_count = pp;
+    free(buf);
+    return bad ? -2 : 0;
+}
+
+/* Montgomery product through one of the reductions: red 0 = Alg. 6, 1 = Alg. 5,
+   3 = Alg. 6 with the truncated Karatsuba high half (Sec. 5.1; n even). */
 static void mont_model(limb *C, const limb *a, const limb *b, const limb *N, const limb *Np, int n,
                        int red, limb *T, limb *Cpre) {
     or_mul(T, a, n, b, n);
     if (red == 0)
         or_montred_alg6(C, Cpre, T, N, Np, n, NULL, NULL);
+    else if (red == 3)
+        or_montred_tkara(C, Cpre, T, N, Np, n, NULL, NULL);
     else
         or_montred_alg5(C, Cpre, T, N, Np, n);
 }
 
 int or_mont_model(limb *C, const limb *a, const limb *b, const limb *N, int n, int red) {
-    if ((N[0] & 1u) == 0) return -1;
+    if ((N[0] & 1u) == 0 || (red == 3 && (n & 1))) return -1;
     limb *Np = (limb *)malloc(sizeof(limb) * (size_t)n);
     limb *T = (limb *)malloc(sizeof(limb) * (size_t)(2 * n));
     limb *Cpre = (limb *)malloc(sizeof(limb) * (size_t)(n + 1));
@@ -402,7 +561,7 @@ int or_mont_model(limb *C, const limb *a, const limb *b, const limb *N, int n, i
  */
 int or_modexp_alg7(limb *y, const limb *a, const limb *e, int ebits, const limb *N, int n, int w,
                    int red) {
-    if ((N[0] & 1u) == 0 || w < 1 || w > 8) return -1;
+    if ((N[0] & 1u) == 0 || w < 1 || w > 8 || (red == 3 && (n & 1))) return -1;
     int E = 1 << w;
     limb *Np = (limb *)malloc(sizeof(limb) * (size_t)n);
     limb *R1 = (limb *)malloc(sizeof(limb) * (size_t)n);

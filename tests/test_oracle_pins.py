@@ -232,6 +232,84 @@ def test_truncated_pp_count(n):
     assert d["pp"] == n * n + 2 * n - 1
 
 
+# ---------------------------------------------------------------- truncated Karatsuba (Sec. 5.1)
+
+def _tkara_check(Nk, T, n, N_words, Np_words):
+    R = 1 << (32 * n)
+    h = n // 2
+    d = oracle.montred_tkara(si.from_int(T, 2 * n), N_words, Np_words)
+    q = (T % R) * si.to_int(Np_words) % R
+    qN = q * Nk
+    assert si.to_int(d["H"]) == qN // R                      # the high half, exactly
+    assert abs(d["e"]) <= 2 * h + 2                          # the estimate's error bound
+    assert d["c_add"] == int(T % R != 0)
+    assert si.to_int(d["Cpre"]) == (T + qN) // R
+    if T < Nk * R:
+        assert si.to_int(d["C"]) == T * pow(R, -1, Nk) % Nk
+    return d
+
+
+@pytest.mark.parametrize("bits", [64, 128, 1000, 2048, 4096])
+def test_truncated_karatsuba_reduction(bits):
+    """Karatsuba form of the truncated reduction: only D2 in full and column estimates of
+    D0 and D1; word n-1 of -T recovers the carry. H must equal floor(qN/R) (Python ints)."""
+    n, N, cases = _reduction_cases(bits, 25, bits + 7)
+    assert n % 2 == 0
+    Np, _, _ = oracle.ctx(N)
+    for k, (Nk, T, R) in enumerate(cases):
+        _tkara_check(Nk, T, n, N[k], Np[k])
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 64])
+def test_truncated_karatsuba_extremes(n):
+    """Carries of every half sum set (N = W^n - 1 gives c_N = 1; q near R gives c_q = 1),
+    T = 0, 1, R, W^2n - 1 and the largest T below N*R."""
+    R = 1 << (32 * n)
+    Ns = [R - 1, (R >> 1) + 1, R - (1 << 32) + 1, si.to_int(si.random_odd_moduli(rng(n + 50), 1, 32 * n)[0])]
+    r = rng(n + 60)
+    for Nk in Ns:
+        Nw = si.from_int(Nk, n)
+        Np = si.from_int((-pow(Nk, -1, R)) % R, n)
+        Ts = [0, 1, R, R * R - 1, Nk * R - 1, (Nk - 1) ** 2, R - 1, (R - 1) * R]
+        Ts += [int.from_bytes(r.bytes(8 * n), "little") for _ in range(6)]
+        for T in Ts:
+            _tkara_check(Nk, T, n, Nw, Np)
+
+
+@pytest.mark.parametrize("n", [2, 4, 32, 64])
+def test_truncated_karatsuba_pp_count(n):
+    """Half products (lo or hi) of the Karatsuba-form reduction: n^2 for q (D0' in full, the
+    low halves of D1' and D2'), 2h^2 for D2 and h^2 + 2h - 1 for each column estimate,
+    2n^2 + 2n - 2 in all: one fewer than the schoolbook truncated reduction's n^2 + (n^2 + 2n - 1).
+    One level of Karatsuba saves nothing on the two half products; the saving is in T = A*B."""
+    N = si.random_odd_moduli(rng(n + 70), 1, 32 * n)
+    Np, _, _ = oracle.ctx(N)
+    T = np.zeros(2 * n, np.uint32)
+    T[0] = 5
+    d = oracle.montred_tkara(T, N[0], Np[0])
+    assert d["pp"] == 2 * n * n + 2 * n - 2
+    # the schoolbook count covers the high half only (n^2 + 2n - 1); q adds n^2
+    assert oracle.montred_alg6(T, N[0], Np[0])["pp"] + n * n == d["pp"] + 1
+    with pytest.raises(ValueError):
+        oracle.montred_tkara(np.zeros(2 * 3, np.uint32), np.array([3, 0, 1], np.uint32), np.zeros(3, np.uint32))
+
+
+@pytest.mark.parametrize("bits", [256, 1024, 2048])
+def test_truncated_karatsuba_products_and_modexp(bits):
+    b = si.make_batch(0, "test", 8, bits, ebits=min(bits, 300), sub=bits + 11)
+    R = 1 << (32 * b.n)
+    got = oracle.mont_model(b.a, b.b, b.N, 3)
+    assert (got == oracle.mont_def(b.a, b.b, b.N)).all()
+    for k in range(8):
+        Nk = si.to_int(b.N[k])
+        assert si.to_int(got[k]) == si.to_int(b.a[k]) * si.to_int(b.b[k]) * pow(R, -1, Nk) % Nk
+    y = oracle.modexp(b.a, b.e, b.ebits, b.N)
+    for w in (1, 5):
+        assert (oracle.modexp_alg7(b.a, b.e, b.ebits, b.N, w, 3) == y).all()
+    with pytest.raises(ValueError):   # odd n has no half split
+        oracle.mont_model(b.a[:, :3], b.b[:, :3], b.N[:, :3] | np.uint32(1), 3)
+
+
 # ---------------------------------------------------------------- exponentiation
 
 @pytest.mark.parametrize("bits", [64, 1024, 2048])
