@@ -292,18 +292,25 @@ def main():
     # word-serial CIOS (Alg. 4) for comparison
     step(mp.RED_CIOS)
     ms_cios = timed(lambda: step(mp.RED_CIOS), max(2, args.steps // 2)) / max(2, args.steps // 2)
+    # truncated reduction in its Karatsuba form (Sec. 5.1) for comparison
+    def step_tk():
+        mp.modexp_consttime(Y, A, E, ebits, ctx, WINDOW, mp.RED_TRUNCATED, mp.ALGO_KARATSUBA, workspace=ws)
+    step_tk()
+    ms_tk = timed(step_tk, max(2, args.steps // 2)) / max(2, args.steps // 2)
+    Y_tk = Y.clone()
 
     # Montgomery products over the same batch
     C = torch.zeros_like(A)
     mm = {}
-    for red, nm in ((mp.RED_TRUNCATED, "trunc"), (mp.RED_FULL, "full"), (mp.RED_CIOS, "cios")):
+    for red, algo, nm in ((mp.RED_TRUNCATED, mp.ALGO_AUTO, "trunc"), (mp.RED_FULL, mp.ALGO_AUTO, "full"),
+                          (mp.RED_CIOS, mp.ALGO_AUTO, "cios"), (mp.RED_TRUNCATED, mp.ALGO_KARATSUBA, "tkara")):
         for _ in range(3):
-            mp.mont_mul(C, A, Bv, ctx, red)
+            mp.mont_mul(C, A, Bv, ctx, red, algo)
         k = 50
-        mm[nm] = world * B / (timed(lambda: mp.mont_mul(C, A, Bv, ctx, red), k) / k / 1e3)
+        mm[nm] = world * B / (timed(lambda: mp.mont_mul(C, A, Bv, ctx, red, algo), k) / k / 1e3)
         for _ in range(3):
-            mp.mont_sqr(C, A, ctx, red)
-        mm[nm + "_sqr"] = world * B / (timed(lambda: mp.mont_sqr(C, A, ctx, red), k) / k / 1e3)
+            mp.mont_sqr(C, A, ctx, red, algo)
+        mm[nm + "_sqr"] = world * B / (timed(lambda: mp.mont_sqr(C, A, ctx, red, algo), k) / k / 1e3)
 
     # end to end through the C ABI with host buffers: H2D inputs, modexp, D2H result
     hA = torch.from_numpy(mp.interleave(b.a).view(np.int32)).pin_memory()
@@ -319,6 +326,8 @@ def main():
 
     e2e_step()
     ms_e2e = timed(e2e_step, args.steps) / args.steps
+    torch.cuda.synchronize()
+    tk_same = bool(torch.equal(Y_tk, Y))   # every instance: Karatsuba form == schoolbook truncated
     h2d = (hA.numel() + hE.numel()) * 4
     d2h = hY.numel() * 4
 
@@ -373,8 +382,11 @@ def main():
             "clocks": clocks,
             "modexp_full_reduction_per_s": world * B / (ms_full / 1e3),
             "modexp_cios_per_s": world * B / (ms_cios / 1e3),
-            "montmul_per_s": {"trunc": mm["trunc"], "full": mm["full"], "cios": mm["cios"]},
-            "montsqr_per_s": {"trunc": mm["trunc_sqr"], "full": mm["full_sqr"], "cios": mm["cios_sqr"]},
+            "modexp_tkara_per_s": world * B / (ms_tk / 1e3),
+            "tkara_equals_schoolbook": tk_same,
+            "montmul_per_s": {"trunc": mm["trunc"], "full": mm["full"], "cios": mm["cios"], "tkara": mm["tkara"]},
+            "montsqr_per_s": {"trunc": mm["trunc_sqr"], "full": mm["full_sqr"], "cios": mm["cios_sqr"],
+                              "tkara": mm["tkara_sqr"]},
             "parity": parity,
             "imad_microbench": {"per_clk_per_sm": imad_rate, "implied_mhz": imad_mhz},
         }
@@ -440,11 +452,12 @@ def bench_4096(args):
     ctx = mp.MontCtx(N, B, 4096, IL)
     C = torch.zeros_like(A)
     mm = {}
-    for red, nm in ((mp.RED_TRUNCATED, "trunc"), (mp.RED_FULL, "full")):
+    for red, algo, nm in ((mp.RED_TRUNCATED, mp.ALGO_AUTO, "trunc"), (mp.RED_FULL, mp.ALGO_AUTO, "full"),
+                          (mp.RED_TRUNCATED, mp.ALGO_KARATSUBA, "tkara")):
         for _ in range(3):
-            mp.mont_mul(C, A, Bv, ctx, red)
-        mm["mul_" + nm] = B / (timed(lambda: mp.mont_mul(C, A, Bv, ctx, red), 20) / 1e3)
-        mm["sqr_" + nm] = B / (timed(lambda: mp.mont_sqr(C, A, ctx, red), 20) / 1e3)
+            mp.mont_mul(C, A, Bv, ctx, red, algo)
+        mm["mul_" + nm] = B / (timed(lambda: mp.mont_mul(C, A, Bv, ctx, red, algo), 20) / 1e3)
+        mm["sqr_" + nm] = B / (timed(lambda: mp.mont_sqr(C, A, ctx, red, algo), 20) / 1e3)
     out["mont_per_s"] = mm
     ws = torch.empty(mp.modexp_workspace_bytes(B, 4096, 6) // 4, dtype=torch.int32, device="cuda")
     Y = torch.zeros_like(A)
@@ -456,6 +469,14 @@ def bench_4096(args):
     idx = np.linspace(0, B - 1, 6).astype(int)
     got = mp.deinterleave(mp.to_host(Y), B, n)[idx]
     want = oracle.modexp(b.a[idx], b.e[idx], b.ebits, b.N[idx])
+    # the same exponentiation with every product in the truncated Karatsuba form (Sec. 5.1)
+    Y_sb = Y.clone()
+    step_tk = lambda: mp.modexp_consttime(Y, A, E, b.ebits, ctx, 6, mp.RED_TRUNCATED, mp.ALGO_KARATSUBA, workspace=ws)
+    step_tk()
+    ms_tk = timed(step_tk, max(2, args.steps))
+    out["modexp_tkara_per_s"] = B / (ms_tk / 1e3)
+    torch.cuda.synchronize()
+    out["tkara_equals_schoolbook"] = bool(torch.equal(Y, Y_sb))
     ctx.free()
     # lazy reduction (no final subtraction while 4N <= W^NP): 4606-bit moduli have the slack
     # in the 144-word shape, 4607-bit ones do not; same shape, same work otherwise

@@ -53,7 +53,9 @@ typedef enum {
 
 typedef enum { MP_LAYOUT_INSTANCE_MAJOR = 0, MP_LAYOUT_INTERLEAVED = 1 } mp_layout;
 /* Products: schoolbook (Alg. 1/2), one level of Karatsuba (Sec. 3), two levels (mp_mul and
-   mp_sqr of the 4096- and 4608-bit classes only; 9 quarter products instead of 16). */
+   mp_sqr of the 4096- and 4608-bit classes only; 9 quarter products instead of 16).
+   For Montgomery products and exponentiation, MP_ALGO_KARATSUBA selects the truncated
+   Karatsuba form (Sec. 5.1; see mont_mul). */
 typedef enum { MP_ALGO_AUTO = 0, MP_ALGO_SCHOOLBOOK = 1, MP_ALGO_KARATSUBA = 2, MP_ALGO_KARATSUBA2 = 3 } mp_algo;
 /* Reductions: truncated (Alg. 6), classical (Alg. 3/5), word-serial CIOS (Alg. 4). */
 typedef enum { MP_RED_TRUNCATED = 0, MP_RED_FULL = 1, MP_RED_CIOS = 2 } mp_red;
@@ -126,6 +128,11 @@ int mont_ctx_export(const mont_ctx *ctx, int which, uint32_t *dst, void *stream)
  * whole T + q*N (Alg. 3, B_fma); MP_RED_CIOS interleaves the product and the
  * reduction word by word (Alg. 4: per word a_i, Y += a_i*B, q = (Y mod W)*n0',
  * Y = (Y + q*N)/W; needs only n0' = N' mod W). All give the same canonical result.
+ * algo: AUTO or SCHOOLBOOK; or KARATSUBA with MP_RED_TRUNCATED for contexts of 1025 to
+ * 2048 and 3073 to 4096 bits (padded sizes 64 and 128 words): T by one Karatsuba level,
+ * q from the low half of a Karatsuba product, and the high half of q*N in the truncated
+ * Karatsuba form of Sec. 5.1 (D2 in full, column estimates of D0 and D1, the missing
+ * carry recovered from word n-1 of -T). Other combinations return MP_ERR_UNIMPLEMENTED.
  * a, b, c: n words per instance in the context layout; c may alias a or b.
  */
 int mont_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, const mont_ctx *ctx, mp_red red,
@@ -151,7 +158,8 @@ size_t modexp_workspace_bytes(size_t batch, uint32_t bits, uint32_t window);
  * ordinary residues (converted to and from the Montgomery domain inside).
  * workspace: device buffer of at least modexp_workspace_bytes(...) bytes, 16-byte
  * aligned; workspace == NULL makes the call allocate and free it on `stream`
- * (stream-ordered allocation). y may alias base.
+ * (stream-ordered allocation). y may alias base. red and algo as for mont_mul (every
+ * product of the exponentiation uses them).
  */
 int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
                      const mont_ctx *ctx, uint32_t window, mp_red red, mp_algo algo,

@@ -22,6 +22,8 @@ ShapeOps shape_ops_8_18();
 ShapeOps shape_ops_8_8_w();
 cudaError_t kara2_128(const KArgs &, cudaStream_t);
 cudaError_t kara2_144(const KArgs &, cudaStream_t);
+ShapeOps tkara_ops_64();
+ShapeOps tkara_ops_128();
 }  // namespace mpg
 
 using namespace mpg;
@@ -43,6 +45,7 @@ struct SizeClass {
     uint32_t window;     // default window for modexp (0: built-in rule)
     uint32_t kara_from;  // AUTO products use Karatsuba from this many bits (0: built-in rule)
     cudaError_t (*kara2)(const KArgs &, cudaStream_t);   // two-level Karatsuba products, or null
+    ShapeOps tk;         // Montgomery products in the truncated Karatsuba form (mont/modexp null if absent)
 };
 static SizeClass g_classes[7];
 static bool g_classes_ready = false;
@@ -56,6 +59,8 @@ static void init_classes() {
     g_classes[4] = SizeClass{96, 2, {shape_ops_8_12(), shape_ops_16_6()}, 0, 0, 0};
     g_classes[5] = SizeClass{128, 2, {shape_ops_16_8(), shape_ops_8_16()}, 0, 0, 0, kara2_128};   // 16x8 faster
     g_classes[6] = SizeClass{144, 1, {shape_ops_8_18()}, 0, 0, 0, kara2_144};
+    g_classes[3].tk = tkara_ops_64();
+    g_classes[5].tk = tkara_ops_128();
     g_classes_ready = true;
 }
 
@@ -382,6 +387,19 @@ static void fill_ctx_args(KArgs &A, const mont_ctx *c) {
 
 void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }
 
+// kernels for a Montgomery product or exponentiation on context c: MP_ALGO_KARATSUBA selects
+// the truncated Karatsuba form (Sec. 5.1), which exists for the truncated reduction of the
+// 2048- and 4096-bit classes; AUTO and SCHOOLBOOK the schoolbook shapes; null otherwise
+static const ShapeOps *ops_for(const mont_ctx *c, mp_red red, mp_algo algo) {
+    if (algo == MP_ALGO_KARATSUBA2) return nullptr;
+    if (algo == MP_ALGO_KARATSUBA) {
+        const SizeClass *cls = class_for(c->np);
+        if (red != MP_RED_TRUNCATED || !cls || !cls->tk.mont || (uint32_t)cls->tk.NP != c->np) return nullptr;
+        return &cls->tk;
+    }
+    return shape_for_red(c->np, (int)red);
+}
+
 static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
                        mp_algo algo, bool square, void *stream) {
     if (!out || !a || (!square && !b) || !c) return MP_ERR_ARG;
@@ -389,13 +407,14 @@ static int mont_common(uint32_t *out, const uint32_t *a, const uint32_t *b, cons
     if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
         algo != MP_ALGO_KARATSUBA2)
         return MP_ERR_ARG;
-    if (algo == MP_ALGO_KARATSUBA || algo == MP_ALGO_KARATSUBA2) return MP_ERR_UNIMPLEMENTED;
+    const ShapeOps *sh = ops_for(c, red, algo);
+    if (!sh) return MP_ERR_UNIMPLEMENTED;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(out) || !aligned16(a) || (!square && !aligned16(b))))
         return MP_ERR_ALIGN;
     KArgs A{};
     fill_ctx_args(A, c);
     A.out = out; A.a = a; A.b = square ? a : b; A.red = (int)red; A.square = square ? 1 : 0;
-    return cuda_status(shape_for_red(c->np, (int)red)->mont(A, S(stream)));
+    return cuda_status(sh->mont(A, S(stream)));
 }
 
 extern "C" int mont_mul(uint32_t *out, const uint32_t *a, const uint32_t *b, const mont_ctx *c, mp_red red,
@@ -474,7 +493,8 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
         algo != MP_ALGO_KARATSUBA2)
         return MP_ERR_ARG;
-    if (algo == MP_ALGO_KARATSUBA || algo == MP_ALGO_KARATSUBA2) return MP_ERR_UNIMPLEMENTED;
+    const ShapeOps *sh = ops_for(c, red, algo);
+    if (!sh) return MP_ERR_UNIMPLEMENTED;
     if (window == 0) window = tuned_window(c->bits);
     if (window > 6) return MP_ERR_SIZE;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp))))
@@ -498,7 +518,7 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     A.out = y; A.a = base; A.e = exp; A.table = reinterpret_cast<uint32_t *>(ws);
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
-    int rc = cuda_status(shape_for_red(c->np, (int)red)->modexp(A, st));
+    int rc = cuda_status(sh->modexp(A, st));
     if (own) {
         if (cudaFreeAsync(ws, st) != cudaSuccess && rc == MP_OK) rc = MP_ERR_CUDA;
     }
@@ -584,7 +604,8 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
     if (algo != MP_ALGO_AUTO && algo != MP_ALGO_SCHOOLBOOK && algo != MP_ALGO_KARATSUBA &&
         algo != MP_ALGO_KARATSUBA2)
         return MP_ERR_ARG;
-    if (algo == MP_ALGO_KARATSUBA || algo == MP_ALGO_KARATSUBA2) return MP_ERR_UNIMPLEMENTED;
+    const ShapeOps *sh = ops_for(c, red, algo);
+    if (!sh) return MP_ERR_UNIMPLEMENTED;
     if (window == 0) window = tuned_window(c->bits);
     if (window > 6) return MP_ERR_SIZE;
     if (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp))))
@@ -598,5 +619,5 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
     A.out = y; A.a = base; A.e = exp; A.table = tables;
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
-    return cuda_status(shape_for_red(c->np, (int)red)->modexp(A, S(stream)));
+    return cuda_status(sh->modexp(A, S(stream)));
 }

@@ -638,12 +638,14 @@ MPG_DI void tri_mac(uint32_t (&Z)[H + 3], const uint32_t *xp, const uint32_t *yp
 //   * the carry into column NP-1 from below is unknown, but word NP-1 of q*N is
 //     known: it is L = ((-T) mod R)[NP-1] (Thm. 1: T + qN = 0 mod R). Hence the
 //     carry out of column NP-1 is floor(Z / W) plus one exactly when L < Z[0].
+//
+// mulhi_sums forms the parts that do not depend on T: the output slots (parked, not yet
+// resolved) and the group sum Z (lane mapping: every thread holds it; warp mapping:
+// thread 0 does).
 template <class S>
-MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, const uint32_t *T,
-                            uint32_t c_add, uint32_t low_zero, uint32_t *C) {
+MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *C, uint32_t (&Z)[S::H + 3]) {
     constexpr int G = S::G, H = S::H, A = S::A2, NP = S::NP;
     // column NP-1 and the hi halves that reach it: thread t takes diagonal blocks u = 2t, 2t+1
-    uint32_t Z[H + 3];
     zero<H + 3>(Z);
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -718,6 +720,14 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
             add_n<H + 3>(Z, o);
         }
     }
+}
+
+template <class S>
+MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, const uint32_t *T,
+                            uint32_t c_add, uint32_t low_zero, uint32_t *C) {
+    constexpr int H = S::H, NP = S::NP;
+    uint32_t Z[H + 3];
+    mulhi_sums<S>(g, Qs, Ns, C, Z);
     // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
     const uint32_t L = ~T[NP - 1] + low_zero;
     const uint32_t extra = (uint32_t)(((uint64_t)L - (uint64_t)Z[0]) >> 63);   // [L < Z[0]]
@@ -727,6 +737,24 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
     add_word<H + 2>(in0, extra + c_add);
     g.sync();
     return resolve<S, H, PAT_ZIGZAG>(g, in0, AddendXform<H>{T + NP}, C);
+}
+
+// Column estimate of floor(X*Y / W^(NP-1)) from the same partial products (the truncated
+// half product of the Karatsuba form, Sec. 5.1): words NP .. 2NP-1 go to C, word NP-1 is
+// returned. Nothing below column NP-1 is known here, so no carry is recovered: the
+// estimate is at most 2*NP below the exact value. Lane mapping only.
+template <class S>
+MPG_DI uint32_t phase_mulhi_est(const Grp<S> &g, const uint32_t *Xs, const uint32_t *Ys, uint32_t *C) {
+    static_assert(!S::WMAP, "estimate: lane mapping only");
+    constexpr int H = S::H;
+    uint32_t Z[H + 3];
+    mulhi_sums<S>(g, Xs, Ys, C, Z);
+    uint32_t in0[H + 2];
+#pragma unroll
+    for (int j = 0; j < H + 2; ++j) in0[j] = Z[1 + j];
+    g.sync();
+    resolve<S, H, PAT_ZIGZAG>(g, in0, NoXform{}, C);
+    return Z[0];
 }
 
 // Classical reduction: T + q*N over all 2*NP words (B_fma), result in T.
@@ -936,12 +964,28 @@ MPG_DI void step_cios(const Grp<S> &g, bool square, bool lazy) {
     if (!lazy) cond_sub<S>(g, g.X(), top, g.N(), g.X());
 }
 
+// Montgomery product with one Karatsuba level and the Karatsuba form of the truncated
+// reduction (mp_tkara.cuh), for its own layouts (KShape).
+template <class S>
+MPG_DI void tk_prepare(const Grp<S> &g);
+template <class S>
+MPG_DI void tk_product(const Grp<S> &g, bool square, bool lazy);
+
+// once per kernel, after N and N' are in shared memory (and synchronised): per-modulus
+// values that the products of reduction RED reuse
+template <class S, int RED>
+MPG_DI void mont_prepare(const Grp<S> &g) {
+    if constexpr (RED == 3) tk_prepare<S>(g);
+}
+
 // X <- X * Y * R^-1 mod N (or X^2 * R^-1 when square): X, Y, N, N' in shared memory.
 // Y is overwritten (it holds q afterwards). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5),
-// 2 word-serial CIOS (Alg. 4).
+// 2 word-serial CIOS (Alg. 4), 3 truncated in its Karatsuba form (Sec. 5.1; KShape layouts).
 template <class S, int RED>
 MPG_DI void mont_mul(const Grp<S> &g, bool square, bool lazy) {
-    if constexpr (RED == 2) {
+    if constexpr (RED == 3) {
+        tk_product<S>(g, square, lazy);
+    } else if constexpr (RED == 2) {
         step_cios<S>(g, square, lazy);
     } else {
         if (square) step_sqr<S>(g);

@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mont(KArgs A
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
     g.sync();
+    mont_prepare<S, RED>(g);
     // one call site; a second product when the internal radix W^NP differs from the
     // API radix W^n: multiply by W^(2NP-n) mod N
     for (int r = 0; r <= (A.correct ? 1 : 0); ++r) {
@@ -295,6 +296,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
         load_ctx<S>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form
     }
     g.sync();
+    mont_prepare<S, RED>(g);
     for (int op = 0; op < nbuild + nwin; ++op) {
         bool square = false;
         if (op >= nbuild) {

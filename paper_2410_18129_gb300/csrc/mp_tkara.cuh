@@ -1,0 +1,217 @@
+// Montgomery product with one level of Karatsuba (Sec. 3) and the truncated reduction in
+// its Karatsuba form (Sec. 5.1), for operands of n = 2h words. Every step runs on the
+// half shape HS (G threads, MH words of a half operand each; h = G*MH):
+//
+//   T   = X*Y = D0 + W^h (D1 - D0 - D2) + W^2h D2             (three half products)
+//   q   = T_lo N' mod R, from the low half of a Karatsuba product only:
+//         D0' = T_l N'_l in full; of D1' = (T_l + T_h)(N'_l + N'_h) and D2' = T_h N'_h only
+//         the low h words: q_l = D0'_l, q_h = D0'_h + D1'_l - D0'_l - D2'_l  (mod W^h)
+//   qN  = W^2h D2 + W^h (D1 - D0 - D2) + D0 with D0 = q_l N_l, D2 = q_h N_h and
+//         D1 = (q_l + q_h)(N_l + N_h) = s_q s_N + W^h (c_q s_N + c_N s_q) + W^2h c_q c_N.
+//         Only D2 is formed in full; D0 and s_q s_N enter through column estimates U0, U1 of
+//         floor(. / W^(h-1)) (phase_mulhi_est), so that
+//           S = W D2 + U1 + W (c_q s_N + c_N s_q) + W^(h+1) c_q c_N - U0
+//               - floor(D2 / W^(h-1)) + floor(U0 / W^h)
+//         estimates floor(qN / W^(n-1)) to within a few units (the paper's truncated form
+//         D2_l + D1_h - D0_h - D2_h + W^h D2_h, one word lower). Word n-1 of qN is known,
+//         L = ((-T) mod R)[n-1] (Thm. 1), so e = (L - S) mod W read as a signed word gives
+//         floor(qN / R) = floor((S + e) / W) exactly.
+//   C   = floor(T / R) + floor(qN / R) + c_add, then the constant-time C - N select.
+//
+// Additions and subtractions run across the group with carry-lookahead (gadd / gsubf);
+// the estimates' low words are group-uniform after the butterfly of phase_mulhi_est.
+#pragma once
+#include "mp_kara.cuh"
+
+namespace mpg {
+
+// Shared-memory map of one instance (32-bit words) for the product over half shape HS_.
+// Besides the full-size operands it keeps the per-modulus half sums s_N (with its carry
+// c_N) and s_N' = N'_l + N'_h mod W^h, formed once per kernel (tk_prepare).
+template <class HS_>
+struct KShape {
+    using HS = HS_;
+    static_assert(!HS::WMAP && HS::MONT_OK, "Karatsuba form: lane-mapped half shape with even MH >= 4");
+    static constexpr int G = HS::G, MH = HS::M, h = HS::NP;
+    static constexpr int M = 2 * MH;              // words per thread of a full operand
+    static constexpr int NP = 2 * h;
+    static constexpr bool WMAP = false;
+    static constexpr bool MONT_OK = true;
+    static constexpr int OFF_X = 0;               // operand / result
+    static constexpr int OFF_Y = NP;              // operand (block squares while squaring)
+    static constexpr int OFF_N = 2 * NP;          // modulus
+    static constexpr int OFF_NI = 3 * NP;         // N' = (-N)^-1 mod R
+    static constexpr int OFF_T = 4 * NP;          // T (2NP words)
+    static constexpr int OFF_SN = 6 * NP;         // s_N = N_l + N_h mod W^h
+    static constexpr int OFF_SNI = OFF_SN + h;    // s_N' = N'_l + N'_h mod W^h
+    static constexpr int OFF_A = OFF_SNI + h;     // scratch (4h words), see tk_product
+    static constexpr int OFF_P = OFF_A + 4 * h;   // slot spills: 2G slots of MH+2 words
+    static constexpr int OFF_Z = OFF_P + 2 * G * (MH + 2);   // M zero words
+    static constexpr int OFF_CN = OFF_Z + M;      // c_N, the carry of N_l + N_h
+    static constexpr int WORDS_RAW = OFF_CN + 1;
+    static constexpr int BANK_RES = G < 16 ? 2 * G : 16;   // instance stride as for Shape
+    static constexpr int WORDS_A = (WORDS_RAW + 3) & ~3;
+    static constexpr int WORDS = WORDS_A + ((BANK_RES - WORDS_A % 32) % 32 + 32) % 32;
+};
+
+// dst[i] = a[i] - b(i) for i < G*C (thread t owns words [t*C, t*C+C)), minus the borrow-in
+// bin (0/1, group-uniform). Returns the borrow out of the top word. b is a functor word
+// index -> word and may read dst: every read happens before the first write.
+template <class S, int C, class BF>
+MPG_DI uint32_t gsubf(const Grp<S> &g, uint32_t *dst, const uint32_t *a, const BF &b, uint32_t bin) {
+    constexpr int G = S::G;
+    uint32_t x[C], y[C];
+    lds<C>(x, a + g.t * C);
+#pragma unroll
+    for (int j = 0; j < C; ++j) y[j] = b(g.t * C + j);
+    uint32_t eq = 0u;
+#pragma unroll
+    for (int j = 0; j < C; ++j) eq |= x[j] ^ y[j];
+    const uint32_t gen = sub_n<C>(x, y);
+    const uint64_t Gm = g.gbits(gen != 0u), Pm = g.gbits(eq == 0u);
+    const uint64_t bw = (Pm + ((Gm << 1) | (uint64_t)bin)) ^ Pm;
+    sub_word<C>(x, (uint32_t)(bw >> g.t) & 1u);
+    gsync();
+    sts<C>(dst + g.t * C, x);
+    gsync();
+    return (uint32_t)(bw >> G) & 1u;
+}
+
+template <class S>
+MPG_DI Grp<typename S::HS> half_view(const Grp<S> &g) {
+    Grp<typename S::HS> gh;
+    gh.sm = g.sm;
+    gh.pa = g.pa;
+    gh.za = g.za;
+    gh.t = g.t;
+    gh.gbase = g.gbase;
+    return gh;
+}
+
+template <class S>
+MPG_DI void tk_prepare(const Grp<S> &g) {
+    using HS = typename S::HS;
+    constexpr int h = S::h, MH = S::MH;
+    const Grp<HS> gh = half_view<S>(g);
+    const uint32_t *N = g.N(), *NI = g.NI();
+    const uint32_t cN = gadd<HS, MH>(gh, g.sm + S::OFF_SN, N, [&](int i) { return N[h + i]; }, 0u);
+    gadd<HS, MH>(gh, g.sm + S::OFF_SNI, NI, [&](int i) { return NI[h + i]; }, 0u);
+    if (g.t == 0) g.sm[S::OFF_CN] = cN;
+    g.sync();
+}
+
+// X <- X * Y * R^-1 mod N (X^2 * R^-1 when square), R = W^NP; Y is overwritten. With lazy,
+// no final subtraction (results below 2N when 4N <= R and the inputs are below 2N).
+// Scratch A (4h words) and the dead halves of X and Y carry the intermediates:
+//   product:    A = [s_X | s_Y | D1 (2h)]                    (squaring: block squares in Y)
+//   q:          A = [q (2h) | -],  X = [s_T | D1'_l],  Y = [D2'_l | -]
+//   high half:  A = [q (2h) | D2 -> floor(qN/R) (2h)],  X = [s_q | U0 words h..2h-1],
+//               Y = [U1 words h..2h-1 | -]
+template <class S>
+MPG_DI void tk_product(const Grp<S> &g, bool square, bool lazy) {
+    using HS = typename S::HS;
+    constexpr int h = S::h, MH = S::MH, NP = S::NP;
+    const Grp<HS> gh = half_view<S>(g);
+    uint32_t *X = g.X(), *Y = g.Y(), *T = g.T(), *A = g.sm + S::OFF_A;
+    const uint32_t *N = g.N(), *NI = g.NI(), *SN = g.sm + S::OFF_SN, *SNI = g.sm + S::OFF_SNI;
+
+    // ---- T = X * Y, one Karatsuba level (Sec. 3)
+    uint32_t *SA = A, *SB = A + h, *D1 = A + 2 * h;
+    const uint32_t ca = gadd<HS, MH>(gh, SA, X, [&](int i) { return X[h + i]; }, 0u);
+    uint32_t cb = ca;
+    if (!square) cb = gadd<HS, MH>(gh, SB, Y, [&](int i) { return Y[h + i]; }, 0u);
+    const uint32_t *sbp = square ? SA : SB;
+    if (square) {
+        phase_sqr<HS>(gh, X, Y, T);              // D0 = X_l^2
+        phase_sqr<HS>(gh, X + h, Y, T + 2 * h);  // D2 = X_h^2
+        phase_sqr<HS>(gh, SA, Y, D1);            // s_X^2
+    } else {
+        phase_mul<HS>(gh, X, Y, T);
+        phase_mul<HS>(gh, X + h, Y + h, T + 2 * h);
+        phase_mul<HS>(gh, SA, SB, D1);
+    }
+    {
+        const uint32_t ma = 0u - ca, mb = 0u - cb;
+        uint32_t top = gadd<HS, 2 * MH>(gh, D1, D1, [&](int i) { return i >= h ? (sbp[i - h] & ma) : 0u; }, 0u);
+        top += gadd<HS, 2 * MH>(gh, D1, D1, [&](int i) { return i >= h ? (SA[i - h] & mb) : 0u; }, 0u);
+        top += ca & cb;
+        top -= gsub<HS, 2 * MH>(gh, D1, D1, T);
+        top -= gsub<HS, 2 * MH>(gh, D1, D1, T + 2 * h);
+        gadd<HS, 4 * MH>(gh, T, T, [&](int i) {
+            return (i >= h && i < 3 * h) ? D1[i - h] : (i == 3 * h ? top : 0u);
+        }, 0u);
+    }
+
+    // ---- c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0], L = ((-T) mod R)[NP-1]
+    uint32_t nz_all = 0u, nz_low = 0u;
+    {
+        uint32_t x[S::M];
+        lds<S::M>(x, T + g.t * S::M);
+#pragma unroll
+        for (int j = 0; j < S::M; ++j) {
+            nz_all |= x[j];
+            if (g.t * S::M + j < NP - 1) nz_low |= x[j];
+        }
+    }
+    const bool pr[2] = {nz_all != 0u, nz_low != 0u};
+    uint32_t mk[2];
+    g.template bits<2>(pr, mk);
+    const uint32_t c_add = mk[0] ? 1u : 0u;
+    const uint32_t L = ~T[NP - 1] + (mk[1] ? 0u : 1u);
+
+    // ---- q = T_lo N' mod R (low half of a Karatsuba product)
+    uint32_t *Q = A, *sT = X, *L1 = X + h, *L2 = Y;
+    phase_mul<HS>(gh, T, NI, Q);                 // D0' = T_l N'_l
+    gadd<HS, MH>(gh, sT, T, [&](int i) { return T[h + i]; }, 0u);
+    phase_mullo<HS>(gh, sT, SNI, L1);            // D1'_l
+    phase_mullo<HS>(gh, T + h, NI + h, L2);      // D2'_l
+    gadd<HS, MH>(gh, Q + h, Q + h, [&](int i) { return L1[i]; }, 0u);
+    gsubf<HS, MH>(gh, Q + h, Q + h, [&](int i) { return L2[i]; }, 0u);
+    gsubf<HS, MH>(gh, Q + h, Q + h, [&](int i) { return Q[i]; }, 0u);
+
+    // ---- floor(qN / R): D2 in full, column estimates of D0 and s_q s_N
+    uint32_t *D2 = A + 2 * h, *sq = X, *C0 = X + h, *C1 = Y;
+    const uint32_t cq = gadd<HS, MH>(gh, sq, Q, [&](int i) { return Q[h + i]; }, 0u);
+    phase_mul<HS>(gh, Q + h, N + h, D2);         // D2 = q_h N_h
+    const uint32_t z0 = phase_mulhi_est<HS>(gh, Q, N, C0);   // U0 = [z0, C0]
+    const uint32_t z1 = phase_mulhi_est<HS>(gh, sq, SN, C1); // U1 = [z1, C1]
+    const uint32_t cN = g.sm[S::OFF_CN];
+    // word n-1 of S (before the error correction) and the carry the correction leaves
+    const int64_t x = (int64_t)z1 - (int64_t)z0 - (int64_t)D2[h - 1] + (int64_t)C0[h - 1];
+    const int32_t e = (int32_t)(L - (uint32_t)x);
+    const int64_t delta = (x + (int64_t)e - (int64_t)L) >> 32;   // exact: x + e = L (mod W)
+    // words n .. 2n-1: D2 - D2_h + U1_hi - U0_hi + c_q s_N + c_N s_q + W^h c_q c_N + delta
+    gsubf<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? D2[h + i] : 0u; }, 0u);
+    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? C1[i] : 0u; }, 0u);
+    gsubf<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? C0[i] : 0u; }, 0u);
+    const uint32_t mq = 0u - cq, mN = 0u - cN;
+    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? (SN[i] & mq) : 0u; }, 0u);
+    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? (sq[i] & mN) : (i == h ? (cq & cN) : 0u); }, 0u);
+    const uint32_t dlo = (uint32_t)delta, dhi = delta < 0 ? 0xffffffffu : 0u;
+    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i == 0 ? dlo : dhi; }, 0u);
+    // C = floor(T / R) + floor(qN / R) + c_add
+    const uint32_t carry = gadd<HS, 2 * MH>(gh, X, T + 2 * h, [&](int i) { return D2[i]; }, c_add);
+    if (!lazy) cond_sub<S>(g, X, carry, N, X);
+}
+
+template <class HS, int TPB>
+struct TKaraImpl {
+    using KS = KShape<HS>;
+    static cudaError_t mont(const KArgs &A, cudaStream_t st) { return launch_k<KS, TPB, 7>(k_mont<KS, TPB, 3>, A, st); }
+    static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
+        return launch_k<KS, TPB, 8>(k_modexp<KS, TPB, 3>, A, st);
+    }
+    static ShapeOps ops() {
+        return ShapeOps{KS::G, KS::M, KS::NP, TPB, (size_t)(TPB / KS::G) * KS::WORDS * 4, nullptr, &mont, &modexp,
+                        nullptr};
+    }
+};
+
+}  // namespace mpg
+
+// Montgomery products and exponentiation of the size class with padded size NP (= 2*G*MH
+// words) in the Karatsuba form, over the half shape (G, MH)
+#define MPG_DEFINE_TKARA(NP, G, MH, TPB)                                                      \
+    namespace mpg {                                                                           \
+    ShapeOps tkara_ops_##NP() { return TKaraImpl<Shape<G, MH>, TPB>::ops(); }                 \
+    }

@@ -329,6 +329,83 @@ def test_karatsuba_auto_and_small_sizes(mp):
     assert e.value.status == -7
 
 
+# ------------------------------------------------------------------ truncated Karatsuba form (Sec. 5.1)
+
+TKARA_SIZES = [1025, 1500, 2046, 2048, 3073, 3500, 4094, 4096]
+
+
+def _tkara_batch(bits, batch, sub):
+    """Random instances plus the extremes: N = 2^bits - 1 (its halves' sum carries), operands
+    0, 1, N-1 and all-ones-like values, exponent 0 and all ones."""
+    b = si.make_batch(0, "test", batch, bits, sub=sub)
+    n = b.n
+    N0 = 2 ** bits - 1
+    b.N[0] = si.from_int(N0, n)
+    b.a[0] = si.from_int(N0 - 1, n)
+    b.b[0] = si.from_int(N0 - 1, n)
+    b.N[1] = si.from_int(2 ** (bits - 1) + 1, n)
+    b.a[1] = si.from_int(1, n)
+    b.b[1] = si.from_int(2 ** (bits - 1), n)
+    b.a[2] = 0
+    b.e[3] = 0
+    b.e[4] = si.from_int(2 ** bits - 1, n)
+    return b
+
+
+@pytest.mark.parametrize("bits", TKARA_SIZES)
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_truncated_karatsuba_mont(mp, bits, layout):
+    """mont_mul / mont_sqr with MP_ALGO_KARATSUBA (T by one Karatsuba level, q from the low half
+    of a Karatsuba product, the high half of qN in the truncated Karatsuba form) against the
+    plain definition; several blocks of instances plus a ragged one."""
+    batch = 83 if bits > 3000 else 203
+    b = _tkara_batch(bits, batch, 8100 + bits)
+    n = b.n
+    ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
+    A, B = dev(mp, b.a, layout), dev(mp, b.b, layout)
+    C = out_tensor(mp, batch, n, layout)
+    mp.mont_mul(C, A, B, ctx, mp.RED_TRUNCATED, mp.ALGO_KARATSUBA)
+    assert_equal(host(mp, C, batch, n, layout), oracle.mont_def(b.a, b.b, b.N), f"tkara mont_mul {bits}")
+    mp.mont_sqr(C, A, ctx, mp.RED_TRUNCATED, mp.ALGO_KARATSUBA)
+    assert_equal(host(mp, C, batch, n, layout), oracle.mont_def(b.a, b.a, b.N), f"tkara mont_sqr {bits}")
+    ctx.free()
+
+
+@pytest.mark.parametrize("bits,batch,window", [(2048, 41, 5), (2046, 37, 4), (1500, 29, 3), (4096, 9, 6),
+                                               (3500, 7, 5)])
+@pytest.mark.parametrize("layout", [IM, IL])
+def test_truncated_karatsuba_modexp(mp, bits, batch, window, layout):
+    """Exponentiation whose every product is in the truncated Karatsuba form (lazy when
+    4N <= W^NP, i.e. 2046 and 1500 bits here), through both allocation paths."""
+    b = _tkara_batch(bits, batch, 8300 + bits)
+    ctx = mp.MontCtx(dev(mp, b.N, layout), batch, bits, layout)
+    want = oracle.modexp(b.a, b.e, b.ebits, b.N)
+    Y = out_tensor(mp, batch, b.n, layout)
+    A, E = dev(mp, b.a, layout), dev(mp, b.e, layout)
+    mp.modexp_consttime(Y, A, E, b.ebits, ctx, window, mp.RED_TRUNCATED, mp.ALGO_KARATSUBA)
+    assert_equal(host(mp, Y, batch, b.n, layout), want, f"tkara modexp {bits}")
+    Y.zero_()
+    mp.modexp_consttime_noalloc(Y, A, E, b.ebits, ctx, window, mp.RED_TRUNCATED, mp.ALGO_KARATSUBA)
+    assert_equal(host(mp, Y, batch, b.n, layout), want, f"tkara modexp noalloc {bits}")
+    ctx.free()
+
+
+def test_truncated_karatsuba_unavailable(mp):
+    """The Karatsuba form exists for the truncated reduction of the 2048- and 4096-bit
+    classes only; everything else reports MP_ERR_UNIMPLEMENTED before any work."""
+    for bits, red in ((1024, 0), (3072, 0), (4108, 0), (2048, 1), (2048, 2), (4096, 1)):
+        b = si.make_batch(0, "test", 4, bits, ebits=8, sub=8500 + bits + red)
+        ctx = mp.MontCtx(dev(mp, b.N, IL), 4, bits, IL)
+        C = out_tensor(mp, 4, b.n, IL)
+        with pytest.raises(mp.MpError) as e:
+            mp.mont_mul(C, dev(mp, b.a, IL), dev(mp, b.b, IL), ctx, red, mp.ALGO_KARATSUBA)
+        assert e.value.status == -7
+        with pytest.raises(mp.MpError) as e:
+            mp.modexp_consttime(C, dev(mp, b.a, IL), dev(mp, b.e, IL), 8, ctx, 4, red, mp.ALGO_KARATSUBA)
+        assert e.value.status == -7
+        ctx.free()
+
+
 # ------------------------------------------------------------------ mixed sizes, one persistent launch
 
 def _mixed_jobs(mp, specs, layout):
