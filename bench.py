@@ -175,6 +175,9 @@ def main():
     ap.add_argument("--reduction", default="truncated", choices=["truncated", "full", "cios"],
                     help="reduction of the timed modexp steps with --quick (profiling); the full line "
                          "always times the truncated one and reports the others beside it")
+    ap.add_argument("--algo", default="auto", choices=["auto", "karatsuba"],
+                    help="product form of the timed modexp steps with --quick: karatsuba runs every "
+                         "Montgomery product in the truncated Karatsuba form")
     ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096", "mixed", "serving"],
                     help="batch_2048: the headline line; batch_4096: 4096-bit products (schoolbook vs "
                          "Karatsuba, 4108/4154 edges), Montgomery and w=6 modexp")
@@ -245,11 +248,12 @@ def main():
         torch.cuda.synchronize()
 
     quick_red = {"truncated": mp.RED_TRUNCATED, "full": mp.RED_FULL, "cios": mp.RED_CIOS}[args.reduction]
-    if not args.quick and quick_red != mp.RED_TRUNCATED:
-        raise SystemExit("--reduction applies to --quick runs only")
+    quick_algo = {"auto": mp.ALGO_AUTO, "karatsuba": mp.ALGO_KARATSUBA}[args.algo]
+    if not args.quick and (quick_red != mp.RED_TRUNCATED or quick_algo != mp.ALGO_AUTO):
+        raise SystemExit("--reduction and --algo apply to --quick runs only")
 
-    def step(red=quick_red):
-        mp.modexp_consttime(Y, A, E, ebits, ctx, WINDOW, red, workspace=ws)
+    def step(red=quick_red, algo=quick_algo):
+        mp.modexp_consttime(Y, A, E, ebits, ctx, WINDOW, red, algo, workspace=ws)
 
     def timed(fn, k):
         barrier()
@@ -281,7 +285,8 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "modexp/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                              "quick": True, "reduction": args.reduction, "batch_per_gpu": B, "clocks": clocks}))
+                              "quick": True, "reduction": args.reduction, "algo": args.algo, "batch_per_gpu": B,
+                              "clocks": clocks}))
         ctx.free()
         return
 

@@ -128,8 +128,8 @@ int mont_ctx_export(const mont_ctx *ctx, int which, uint32_t *dst, void *stream)
  * whole T + q*N (Alg. 3, B_fma); MP_RED_CIOS interleaves the product and the
  * reduction word by word (Alg. 4: per word a_i, Y += a_i*B, q = (Y mod W)*n0',
  * Y = (Y + q*N)/W; needs only n0' = N' mod W). All give the same canonical result.
- * algo: AUTO or SCHOOLBOOK; or KARATSUBA with MP_RED_TRUNCATED for contexts of 1025 to
- * 2048 and 3073 to 4096 bits (padded sizes 64 and 128 words): T by one Karatsuba level,
+ * algo: AUTO or SCHOOLBOOK; or KARATSUBA with MP_RED_TRUNCATED for contexts of 257 to
+ * 4096 bits (padded sizes 16 to 128 words): T by one Karatsuba level,
  * q from the low half of a Karatsuba product, and the high half of q*N in the truncated
  * Karatsuba form of Sec. 5.1 (D2 in full, column estimates of D0 and D1, the missing
  * carry recovered from word n-1 of -T). Other combinations return MP_ERR_UNIMPLEMENTED.

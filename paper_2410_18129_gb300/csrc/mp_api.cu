@@ -22,7 +22,10 @@ ShapeOps shape_ops_8_18();
 ShapeOps shape_ops_8_8_w();
 cudaError_t kara2_128(const KArgs &, cudaStream_t);
 cudaError_t kara2_144(const KArgs &, cudaStream_t);
+ShapeOps tkara_ops_16();
+ShapeOps tkara_ops_32();
 ShapeOps tkara_ops_64();
+ShapeOps tkara_ops_96();
 ShapeOps tkara_ops_128();
 }  // namespace mpg
 
@@ -59,8 +62,11 @@ static void init_classes() {
     g_classes[4] = SizeClass{96, 2, {shape_ops_8_12(), shape_ops_16_6()}, 0, 0, 0};
     g_classes[5] = SizeClass{128, 2, {shape_ops_16_8(), shape_ops_8_16()}, 0, 0, 0, kara2_128};   // 16x8 faster
     g_classes[6] = SizeClass{144, 1, {shape_ops_8_18()}, 0, 0, 0, kara2_144};
+    g_classes[1].tk = tkara_ops_16();    // the 256-bit class has no half shape (2 x 2 words)
+    g_classes[2].tk = tkara_ops_32();
     g_classes[3].tk = tkara_ops_64();
-    g_classes[5].tk = tkara_ops_128();
+    g_classes[4].tk = tkara_ops_96();
+    g_classes[5].tk = tkara_ops_128();   // the 4608-bit class neither (8 x 9 has odd half blocks)
     g_classes_ready = true;
 }
 
@@ -389,7 +395,7 @@ void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }
 
 // kernels for a Montgomery product or exponentiation on context c: MP_ALGO_KARATSUBA selects
 // the truncated Karatsuba form (Sec. 5.1), which exists for the truncated reduction of the
-// 2048- and 4096-bit classes; AUTO and SCHOOLBOOK the schoolbook shapes; null otherwise
+// classes from 512 to 4096 bits; AUTO and SCHOOLBOOK the schoolbook shapes; null otherwise
 static const ShapeOps *ops_for(const mont_ctx *c, mp_red red, mp_algo algo) {
     if (algo == MP_ALGO_KARATSUBA2) return nullptr;
     if (algo == MP_ALGO_KARATSUBA) {

@@ -18,7 +18,7 @@
 //         floor(qN / R) = floor((S + e) / W) exactly.
 //   C   = floor(T / R) + floor(qN / R) + c_add, then the constant-time C - N select.
 //
-// Additions and subtractions run across the group with carry-lookahead (gadd / gsubf);
+// Additions and subtractions run across the group with carry-lookahead (gadd / gsumk);
 // the estimates' low words are group-uniform after the butterfly of phase_mulhi_est.
 #pragma once
 #include "mp_kara.cuh"
@@ -54,27 +54,46 @@ struct KShape {
     static constexpr int WORDS = WORDS_A + ((BANK_RES - WORDS_A % 32) % 32 + 32) % 32;
 };
 
-// dst[i] = a[i] - b(i) for i < G*C (thread t owns words [t*C, t*C+C)), minus the borrow-in
-// bin (0/1, group-uniform). Returns the borrow out of the top word. b is a functor word
-// index -> word and may read dst: every read happens before the first write.
-template <class S, int C, class BF>
-MPG_DI uint32_t gsubf(const Grp<S> &g, uint32_t *dst, const uint32_t *a, const BF &b, uint32_t bin) {
+// dst[i] = (c0 + sum over k < K of term(i, k)) mod W^(G*C) for i < G*C (thread t owns words
+// [t*C, t*C+C)); returns the sum divided by W^(G*C) (group-uniform). A subtraction enters as
+// the complemented word ~y (over all G*C words) with its +1 in c0. Each thread adds its K
+// terms with carry chains into a carry word (< K), passes that word to the next thread
+// (thread 0 takes c0) and adds the one it receives; the remaining one-bit carries are resolved
+// across the group with the carry-lookahead. term may read dst: every read comes before the
+// first write.
+template <class S, int C, int K, class TF>
+MPG_DI uint32_t gsumk(const Grp<S> &g, uint32_t *dst, const TF &term, uint32_t c0) {
     constexpr int G = S::G;
+    const int w0 = g.t * C;
     uint32_t x[C], y[C];
-    lds<C>(x, a + g.t * C);
 #pragma unroll
-    for (int j = 0; j < C; ++j) y[j] = b(g.t * C + j);
-    uint32_t eq = 0u;
+    for (int j = 0; j < C; ++j) x[j] = term(w0 + j, 0);
+    uint32_t top = 0u;
 #pragma unroll
-    for (int j = 0; j < C; ++j) eq |= x[j] ^ y[j];
-    const uint32_t gen = sub_n<C>(x, y);
-    const uint64_t Gm = g.gbits(gen != 0u), Pm = g.gbits(eq == 0u);
-    const uint64_t bw = (Pm + ((Gm << 1) | (uint64_t)bin)) ^ Pm;
-    sub_word<C>(x, (uint32_t)(bw >> g.t) & 1u);
+    for (int k = 1; k < K; ++k) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) y[j] = term(w0 + j, k);
+        add_cc(x[0], y[0]);
+#pragma unroll
+        for (int j = 1; j < C; ++j) addc_cc(x[j], y[j]);
+        addc(top, 0u);
+    }
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, top, 1);
+    add_cc(x[0], g.t == 0 ? c0 : prev);
+#pragma unroll
+    for (int j = 1; j < C; ++j) addc_cc(x[j], 0u);
+    const uint32_t gen = addc_get();
+    uint32_t all = x[0];
+#pragma unroll
+    for (int j = 1; j < C; ++j) all &= x[j];
+    const uint64_t Gm = g.gbits(gen != 0u), Pm = g.gbits(all == 0xffffffffu);
+    const uint64_t cin = (Pm + (Gm << 1)) ^ Pm;
+    add_word<C>(x, (uint32_t)(cin >> g.t) & 1u);
+    const uint32_t last = __shfl_sync(0xffffffffu, top, g.gbase + G - 1);
     gsync();
-    sts<C>(dst + g.t * C, x);
+    sts<C>(dst + w0, x);
     gsync();
-    return (uint32_t)(bw >> G) & 1u;
+    return last + ((uint32_t)(cin >> G) & 1u);
 }
 
 template <class S>
@@ -131,15 +150,20 @@ MPG_DI void tk_product(const Grp<S> &g, bool square, bool lazy) {
         phase_mul<HS>(gh, SA, SB, D1);
     }
     {
-        const uint32_t ma = 0u - ca, mb = 0u - cb;
-        uint32_t top = gadd<HS, 2 * MH>(gh, D1, D1, [&](int i) { return i >= h ? (sbp[i - h] & ma) : 0u; }, 0u);
-        top += gadd<HS, 2 * MH>(gh, D1, D1, [&](int i) { return i >= h ? (SA[i - h] & mb) : 0u; }, 0u);
-        top += ca & cb;
-        top -= gsub<HS, 2 * MH>(gh, D1, D1, T);
-        top -= gsub<HS, 2 * MH>(gh, D1, D1, T + 2 * h);
-        gadd<HS, 4 * MH>(gh, T, T, [&](int i) {
-            return (i >= h && i < 3 * h) ? D1[i - h] : (i == 3 * h ? top : 0u);
-        }, 0u);
+        // T[h .. 4h) += D1 + W^h (c_a s_b + c_b s_a) + W^2h c_a c_b - D0 - D2   (one pass, mod W^3h;
+        // the middle term is >= 0 and T < W^4h, so the window holds the exact words)
+        const uint32_t ma = 0u - ca, mb = 0u - cb, cc = ca & cb;
+        uint32_t *TW = T + h;
+        gsumk<HS, 3 * MH, 6>(gh, TW, [&](int j, int k) -> uint32_t {
+            switch (k) {
+                case 0: return TW[j];
+                case 1: return j < 2 * h ? D1[j] : 0u;
+                case 2: return (j >= h && j < 2 * h) ? (sbp[j - h] & ma) : (j == 2 * h ? cc : 0u);
+                case 3: return (j >= h && j < 2 * h) ? (SA[j - h] & mb) : 0u;
+                case 4: return j < 2 * h ? ~T[j] : 0xffffffffu;            // - D0
+                default: return j < 2 * h ? ~T[2 * h + j] : 0xffffffffu;   // - D2
+            }
+        }, 2u);
     }
 
     // ---- c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0], L = ((-T) mod R)[NP-1]
@@ -165,9 +189,14 @@ MPG_DI void tk_product(const Grp<S> &g, bool square, bool lazy) {
     gadd<HS, MH>(gh, sT, T, [&](int i) { return T[h + i]; }, 0u);
     phase_mullo<HS>(gh, sT, SNI, L1);            // D1'_l
     phase_mullo<HS>(gh, T + h, NI + h, L2);      // D2'_l
-    gadd<HS, MH>(gh, Q + h, Q + h, [&](int i) { return L1[i]; }, 0u);
-    gsubf<HS, MH>(gh, Q + h, Q + h, [&](int i) { return L2[i]; }, 0u);
-    gsubf<HS, MH>(gh, Q + h, Q + h, [&](int i) { return Q[i]; }, 0u);
+    gsumk<HS, MH, 4>(gh, Q + h, [&](int j, int k) -> uint32_t {   // q_h = D0'_h + D1'_l - D0'_l - D2'_l
+        switch (k) {
+            case 0: return Q[h + j];
+            case 1: return L1[j];
+            case 2: return ~Q[j];
+            default: return ~L2[j];
+        }
+    }, 2u);
 
     // ---- floor(qN / R): D2 in full, column estimates of D0 and s_q s_N
     uint32_t *D2 = A + 2 * h, *sq = X, *C0 = X + h, *C1 = Y;
@@ -180,17 +209,25 @@ MPG_DI void tk_product(const Grp<S> &g, bool square, bool lazy) {
     const int64_t x = (int64_t)z1 - (int64_t)z0 - (int64_t)D2[h - 1] + (int64_t)C0[h - 1];
     const int32_t e = (int32_t)(L - (uint32_t)x);
     const int64_t delta = (x + (int64_t)e - (int64_t)L) >> 32;   // exact: x + e = L (mod W)
-    // words n .. 2n-1: D2 - D2_h + U1_hi - U0_hi + c_q s_N + c_N s_q + W^h c_q c_N + delta
-    gsubf<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? D2[h + i] : 0u; }, 0u);
-    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? C1[i] : 0u; }, 0u);
-    gsubf<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? C0[i] : 0u; }, 0u);
+    // C = floor(T / R) + floor(qN / R) + c_add in one pass, with
+    //   floor(qN / R) = D2 - D2_h + U1_hi - U0_hi + c_q s_N + c_N s_q + W^h c_q c_N + delta.
+    // The two complemented terms add 2 R and a negative delta (sign-extended) one more R to
+    // the sum; the carry out of C is what is left above them.
     const uint32_t mq = 0u - cq, mN = 0u - cN;
-    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? (SN[i] & mq) : 0u; }, 0u);
-    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i < h ? (sq[i] & mN) : (i == h ? (cq & cN) : 0u); }, 0u);
     const uint32_t dlo = (uint32_t)delta, dhi = delta < 0 ? 0xffffffffu : 0u;
-    gadd<HS, 2 * MH>(gh, D2, D2, [&](int i) { return i == 0 ? dlo : dhi; }, 0u);
-    // C = floor(T / R) + floor(qN / R) + c_add
-    const uint32_t carry = gadd<HS, 2 * MH>(gh, X, T + 2 * h, [&](int i) { return D2[i]; }, c_add);
+    const uint32_t tot = gsumk<HS, 2 * MH, 8>(gh, X, [&](int i, int k) -> uint32_t {
+        switch (k) {
+            case 0: return T[2 * h + i];
+            case 1: return D2[i];
+            case 2: return i < h ? ~D2[h + i] : 0xffffffffu;
+            case 3: return i < h ? C1[i] : 0u;
+            case 4: return i < h ? ~C0[i] : 0xffffffffu;
+            case 5: return i < h ? (SN[i] & mq) : 0u;
+            case 6: return i < h ? (sq[i] & mN) : (i == h ? (cq & cN) : 0u);
+            default: return i == 0 ? dlo : dhi;
+        }
+    }, 2u + c_add);
+    const uint32_t carry = tot - 2u - (delta < 0 ? 1u : 0u);
     if (!lazy) cond_sub<S>(g, X, carry, N, X);
 }
 

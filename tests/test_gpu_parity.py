@@ -331,7 +331,7 @@ def test_karatsuba_auto_and_small_sizes(mp):
 
 # ------------------------------------------------------------------ truncated Karatsuba form (Sec. 5.1)
 
-TKARA_SIZES = [1025, 1500, 2046, 2048, 3073, 3500, 4094, 4096]
+TKARA_SIZES = [257, 512, 513, 1000, 1024, 1025, 1500, 2046, 2048, 2100, 3072, 3073, 3500, 4094, 4096]
 
 
 def _tkara_batch(bits, batch, sub):
@@ -372,7 +372,8 @@ def test_truncated_karatsuba_mont(mp, bits, layout):
 
 
 @pytest.mark.parametrize("bits,batch,window", [(2048, 41, 5), (2046, 37, 4), (1500, 29, 3), (4096, 9, 6),
-                                               (3500, 7, 5)])
+                                               (3500, 7, 5), (1024, 70, 4), (3072, 13, 5), (512, 90, 4),
+                                               (300, 33, 3)])
 @pytest.mark.parametrize("layout", [IM, IL])
 def test_truncated_karatsuba_modexp(mp, bits, batch, window, layout):
     """Exponentiation whose every product is in the truncated Karatsuba form (lazy when
@@ -391,9 +392,10 @@ def test_truncated_karatsuba_modexp(mp, bits, batch, window, layout):
 
 
 def test_truncated_karatsuba_unavailable(mp):
-    """The Karatsuba form exists for the truncated reduction of the 2048- and 4096-bit
-    classes only; everything else reports MP_ERR_UNIMPLEMENTED before any work."""
-    for bits, red in ((1024, 0), (3072, 0), (4108, 0), (2048, 1), (2048, 2), (4096, 1)):
+    """The Karatsuba form exists for the truncated reduction of the classes from 512 to 4096
+    bits; the 256- and 4608-bit classes and the other reductions report MP_ERR_UNIMPLEMENTED
+    before any work."""
+    for bits, red in ((256, 0), (100, 0), (4108, 0), (4608, 0), (2048, 1), (2048, 2), (4096, 1), (1024, 2)):
         b = si.make_batch(0, "test", 4, bits, ebits=8, sub=8500 + bits + red)
         ctx = mp.MontCtx(dev(mp, b.N, IL), 4, bits, IL)
         C = out_tensor(mp, 4, b.n, IL)
