@@ -133,82 +133,98 @@ MPG_DI void tk_product(const Grp<S> &g, bool square, bool lazy) {
     const Grp<HS> gh = half_view<S>(g);
     uint32_t *X = g.X(), *Y = g.Y(), *T = g.T(), *A = g.sm + S::OFF_A;
     const uint32_t *N = g.N(), *NI = g.NI(), *SN = g.sm + S::OFF_SN, *SNI = g.sm + S::OFF_SNI;
+    uint32_t *SA = A, *SB = A + h, *D1 = A + 2 * h;       // product
+    uint32_t *Q = A, *sT = X, *L1 = X + h, *L2 = Y;       // q
+    uint32_t *D2 = A + 2 * h, *sq = X, *C0 = X + h, *C1 = Y;   // high half of qN
+    uint32_t ca = 0u, cb = 0u, c_add = 0u, L = 0u, cq = 0u, z0 = 0u, z1 = 0u;
 
-    // ---- T = X * Y, one Karatsuba level (Sec. 3)
-    uint32_t *SA = A, *SB = A + h, *D1 = A + 2 * h;
-    const uint32_t ca = gadd<HS, MH>(gh, SA, X, [&](int i) { return X[h + i]; }, 0u);
-    uint32_t cb = ca;
-    if (!square) cb = gadd<HS, MH>(gh, SB, Y, [&](int i) { return Y[h + i]; }, 0u);
-    const uint32_t *sbp = square ? SA : SB;
-    if (square) {
-        phase_sqr<HS>(gh, X, Y, T);              // D0 = X_l^2
-        phase_sqr<HS>(gh, X + h, Y, T + 2 * h);  // D2 = X_h^2
-        phase_sqr<HS>(gh, SA, Y, D1);            // s_X^2
-    } else {
-        phase_mul<HS>(gh, X, Y, T);
-        phase_mul<HS>(gh, X + h, Y + h, T + 2 * h);
-        phase_mul<HS>(gh, SA, SB, D1);
-    }
-    {
-        // T[h .. 4h) += D1 + W^h (c_a s_b + c_b s_a) + W^2h c_a c_b - D0 - D2   (one pass, mod W^3h;
-        // the middle term is >= 0 and T < W^4h, so the window holds the exact words)
-        const uint32_t ma = 0u - ca, mb = 0u - cb, cc = ca & cb;
-        uint32_t *TW = T + h;
-        gsumk<HS, 3 * MH, 6>(gh, TW, [&](int j, int k) -> uint32_t {
-            switch (k) {
-                case 0: return TW[j];
-                case 1: return j < 2 * h ? D1[j] : 0u;
-                case 2: return (j >= h && j < 2 * h) ? (sbp[j - h] & ma) : (j == 2 * h ? cc : 0u);
-                case 3: return (j >= h && j < 2 * h) ? (SA[j - h] & mb) : 0u;
-                case 4: return j < 2 * h ? ~T[j] : 0xffffffffu;            // - D0
-                default: return j < 2 * h ? ~T[2 * h + j] : 0xffffffffu;   // - D2
-            }
-        }, 2u);
-    }
-
-    // ---- c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0], L = ((-T) mod R)[NP-1]
-    uint32_t nz_all = 0u, nz_low = 0u;
-    {
-        uint32_t x[S::M];
-        lds<S::M>(x, T + g.t * S::M);
+    // The nine half products run from one loop, so each kind of product (full, square, low
+    // half, column estimate) and each step between them is inlined once:
+    //   0 D0 = X_l Y_l   1 D2 = X_h Y_h   2 D1 = s_X s_Y          (squares when squaring)
+    //   3 D0' = T_l N'_l   4 D1'_l = s_T s_N' mod W^h   5 D2'_l = T_h N'_h mod W^h
+    //   6 D2 = q_h N_h   7 U0 ~ q_l N_l / W^(h-1)   8 U1 ~ s_q s_N / W^(h-1)
+    MPG_BLOCK_LOOP
+    for (int st = 0; st < 9; ++st) {
+        if (st == 0) {
+            ca = gadd<HS, MH>(gh, SA, X, [&](int i) { return X[h + i]; }, 0u);
+            cb = ca;
+            if (!square) cb = gadd<HS, MH>(gh, SB, Y, [&](int i) { return Y[h + i]; }, 0u);
+        } else if (st == 3) {
+            // T[h .. 4h) += D1 + W^h (c_a s_b + c_b s_a) + W^2h c_a c_b - D0 - D2   (one pass, mod
+            // W^3h; the middle term is >= 0 and T < W^4h, so the window holds the exact words)
+            const uint32_t *sbp = square ? SA : SB;
+            const uint32_t ma = 0u - ca, mb = 0u - cb, cc = ca & cb;
+            uint32_t *TW = T + h;
+            gsumk<HS, 3 * MH, 6>(gh, TW, [&](int j, int k) -> uint32_t {
+                switch (k) {
+                    case 0: return TW[j];
+                    case 1: return j < 2 * h ? D1[j] : 0u;
+                    case 2: return (j >= h && j < 2 * h) ? (sbp[j - h] & ma) : (j == 2 * h ? cc : 0u);
+                    case 3: return (j >= h && j < 2 * h) ? (SA[j - h] & mb) : 0u;
+                    case 4: return j < 2 * h ? ~T[j] : 0xffffffffu;            // - D0
+                    default: return j < 2 * h ? ~T[2 * h + j] : 0xffffffffu;   // - D2
+                }
+            }, 2u);
+            // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0], L = ((-T) mod R)[NP-1]
+            uint32_t nz_all = 0u, nz_low = 0u;
+            {
+                uint32_t x[S::M];
+                lds<S::M>(x, T + g.t * S::M);
 #pragma unroll
-        for (int j = 0; j < S::M; ++j) {
-            nz_all |= x[j];
-            if (g.t * S::M + j < NP - 1) nz_low |= x[j];
+                for (int j = 0; j < S::M; ++j) {
+                    nz_all |= x[j];
+                    if (g.t * S::M + j < NP - 1) nz_low |= x[j];
+                }
+            }
+            const bool pr[2] = {nz_all != 0u, nz_low != 0u};
+            uint32_t mk[2];
+            g.template bits<2>(pr, mk);
+            c_add = mk[0] ? 1u : 0u;
+            L = ~T[NP - 1] + (mk[1] ? 0u : 1u);
+        } else if (st == 4) {
+            gadd<HS, MH>(gh, sT, T, [&](int i) { return T[h + i]; }, 0u);
+        } else if (st == 6) {
+            gsumk<HS, MH, 4>(gh, Q + h, [&](int j, int k) -> uint32_t {   // q_h = D0'_h + D1'_l - D0'_l - D2'_l
+                switch (k) {
+                    case 0: return Q[h + j];
+                    case 1: return L1[j];
+                    case 2: return ~Q[j];
+                    default: return ~L2[j];
+                }
+            }, 2u);
+            cq = gadd<HS, MH>(gh, sq, Q, [&](int i) { return Q[h + i]; }, 0u);
+        }
+        const uint32_t *x, *y;
+        uint32_t *o;
+        switch (st) {
+            case 0: x = X; y = Y; o = T; break;
+            case 1: x = X + h; y = Y + h; o = T + 2 * h; break;
+            case 2: x = SA; y = SB; o = D1; break;
+            case 3: x = T; y = NI; o = Q; break;
+            case 4: x = sT; y = SNI; o = L1; break;
+            case 5: x = T + h; y = NI + h; o = L2; break;
+            case 6: x = Q + h; y = N + h; o = D2; break;
+            case 7: x = Q; y = N; o = C0; break;
+            default: x = sq; y = SN; o = C1; break;
+        }
+        if (st < 3 && square) {
+            phase_sqr<HS>(gh, x, Y, o);          // block squares in Y (free while squaring)
+        } else if (st < 4 || st == 6) {
+            phase_mul<HS>(gh, x, y, o);
+        } else if (st < 6) {
+            phase_mullo<HS>(gh, x, y, o);
+        } else {
+            const uint32_t z = phase_mulhi_est<HS>(gh, x, y, o);
+            if (st == 7) z0 = z;
+            else z1 = z;
         }
     }
-    const bool pr[2] = {nz_all != 0u, nz_low != 0u};
-    uint32_t mk[2];
-    g.template bits<2>(pr, mk);
-    const uint32_t c_add = mk[0] ? 1u : 0u;
-    const uint32_t L = ~T[NP - 1] + (mk[1] ? 0u : 1u);
 
-    // ---- q = T_lo N' mod R (low half of a Karatsuba product)
-    uint32_t *Q = A, *sT = X, *L1 = X + h, *L2 = Y;
-    phase_mul<HS>(gh, T, NI, Q);                 // D0' = T_l N'_l
-    gadd<HS, MH>(gh, sT, T, [&](int i) { return T[h + i]; }, 0u);
-    phase_mullo<HS>(gh, sT, SNI, L1);            // D1'_l
-    phase_mullo<HS>(gh, T + h, NI + h, L2);      // D2'_l
-    gsumk<HS, MH, 4>(gh, Q + h, [&](int j, int k) -> uint32_t {   // q_h = D0'_h + D1'_l - D0'_l - D2'_l
-        switch (k) {
-            case 0: return Q[h + j];
-            case 1: return L1[j];
-            case 2: return ~Q[j];
-            default: return ~L2[j];
-        }
-    }, 2u);
-
-    // ---- floor(qN / R): D2 in full, column estimates of D0 and s_q s_N
-    uint32_t *D2 = A + 2 * h, *sq = X, *C0 = X + h, *C1 = Y;
-    const uint32_t cq = gadd<HS, MH>(gh, sq, Q, [&](int i) { return Q[h + i]; }, 0u);
-    phase_mul<HS>(gh, Q + h, N + h, D2);         // D2 = q_h N_h
-    const uint32_t z0 = phase_mulhi_est<HS>(gh, Q, N, C0);   // U0 = [z0, C0]
-    const uint32_t z1 = phase_mulhi_est<HS>(gh, sq, SN, C1); // U1 = [z1, C1]
     const uint32_t cN = g.sm[S::OFF_CN];
     // word n-1 of S (before the error correction) and the carry the correction leaves
-    const int64_t x = (int64_t)z1 - (int64_t)z0 - (int64_t)D2[h - 1] + (int64_t)C0[h - 1];
-    const int32_t e = (int32_t)(L - (uint32_t)x);
-    const int64_t delta = (x + (int64_t)e - (int64_t)L) >> 32;   // exact: x + e = L (mod W)
+    const int64_t xs = (int64_t)z1 - (int64_t)z0 - (int64_t)D2[h - 1] + (int64_t)C0[h - 1];
+    const int32_t e = (int32_t)(L - (uint32_t)xs);
+    const int64_t delta = (xs + (int64_t)e - (int64_t)L) >> 32;   // exact: xs + e = L (mod W)
     // C = floor(T / R) + floor(qN / R) + c_add in one pass, with
     //   floor(qN / R) = D2 - D2_h + U1_hi - U0_hi + c_q s_N + c_N s_q + W^h c_q c_N + delta.
     // The two complemented terms add 2 R and a negative delta (sign-extended) one more R to
