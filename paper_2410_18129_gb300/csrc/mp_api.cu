@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include "mp_internal.h"
 
@@ -51,10 +52,9 @@ struct SizeClass {
     ShapeOps tk;         // Montgomery products in the truncated Karatsuba form (mont/modexp null if absent)
 };
 static SizeClass g_classes[7];
-static bool g_classes_ready = false;
+static std::once_flag g_classes_once;
 
-static void init_classes() {
-    if (g_classes_ready) return;
+static void fill_classes() {
     g_classes[0] = SizeClass{8, 1, {shape_ops_2_4()}, 0, 0, 0};
     g_classes[1] = SizeClass{16, 1, {shape_ops_4_4()}, 0, 0, 0};
     g_classes[2] = SizeClass{32, 2, {shape_ops_4_8(), shape_ops_8_4()}, 0, 0, 0};
@@ -67,8 +67,9 @@ static void init_classes() {
     g_classes[3].tk = tkara_ops_64();
     g_classes[4].tk = tkara_ops_96();
     g_classes[5].tk = tkara_ops_128();   // the 4608-bit class neither (8 x 9 has odd half blocks)
-    g_classes_ready = true;
 }
+
+static void init_classes() { std::call_once(g_classes_once, fill_classes); }
 
 static SizeClass *class_for(uint32_t n) {
     init_classes();

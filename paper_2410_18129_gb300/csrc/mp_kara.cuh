@@ -247,12 +247,9 @@ static cudaError_t launch_kara2(const KArgs &A, cudaStream_t st) {
     using L = Kara2Layout<QS>;
     constexpr int GPB = TPB / QS::G;
     const size_t smem = (size_t)GPB * L::WORDS * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_kara2<QS, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0ull};
+    const cudaError_t e = smem_attr_once(attr_done, k_kara2<QS, TPB>, smem);
+    if (e != cudaSuccess) return e;
     const size_t blocks = (A.batch + GPB - 1) / GPB;
     k_kara2<QS, TPB><<<(unsigned)blocks, TPB, smem, st>>>(A);
     return cudaGetLastError();
@@ -263,12 +260,9 @@ static cudaError_t launch_kara(const KArgs &A, cudaStream_t st) {
     using L = KaraLayout<F, HS>;
     constexpr int GPB = TPB / F::G;
     const size_t smem = (size_t)GPB * L::WORDS * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_kara<F, HS, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0ull};
+    const cudaError_t e = smem_attr_once(attr_done, k_kara<F, HS, TPB>, smem);
+    if (e != cudaSuccess) return e;
     const size_t blocks = (A.batch + GPB - 1) / GPB;
     k_kara<F, HS, TPB><<<(unsigned)blocks, TPB, smem, st>>>(A);
     return cudaGetLastError();

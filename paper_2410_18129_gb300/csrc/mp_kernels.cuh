@@ -3,6 +3,7 @@
 // its own translation unit (mp_shape_*.cu) and exposed through a ShapeOps table.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include "mp_group.cuh"
 
@@ -368,17 +369,30 @@ struct ShapeOps {
     cudaError_t (*kara)(const KArgs &, cudaStream_t);   // one-level Karatsuba product, or null
 };
 
+// Allow `smem` bytes of dynamic shared memory for kern on the current device, once per kernel
+// and device (function attributes belong to a device's context, so a process that drives several
+// GPUs sets each). done: one bit per device; two threads that race on a first call both set the
+// attribute, which is harmless.
+template <class F>
+static cudaError_t smem_attr_once(std::atomic<unsigned long long> &done, F kern, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 // KIND tells the kernels of one shape apart, so that each gets its own attribute call
 template <class S, int TPB, int KIND, class F>
 static cudaError_t launch_k(F kern, const KArgs &A, cudaStream_t st) {
     constexpr int GPB = TPB / S::G;
     const size_t smem = (size_t)GPB * S::WORDS * 4;
-    static bool attr_set = false;   // one attribute call per kernel and process
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0ull};
+    const cudaError_t e = smem_attr_once(attr_done, kern, smem);
+    if (e != cudaSuccess) return e;
     const size_t blocks = (A.batch + GPB - 1) / GPB;
     kern<<<(unsigned)blocks, TPB, smem, st>>>(A);
     return cudaGetLastError();

@@ -11,6 +11,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <atomic>
 #include "mp_internal.h"
 
 namespace mpg {
@@ -87,18 +88,22 @@ __global__ void __launch_bounds__(MIX_TPB, 2) k_modexp_mixed(const __grid_consta
 
 template <int RED>
 cudaError_t launch_mixed(const MixArgs &P, cudaStream_t st) {
-    static int grid = 0;   // resident blocks over the whole GPU, computed once per process
+    // resident blocks over the whole GPU, computed once per device (with its attribute call)
+    static std::atomic<int> grids[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int grid = (dev >= 0 && dev < 64) ? grids[dev].load(std::memory_order_acquire) : 0;
     if (!grid) {
-        cudaError_t e = cudaFuncSetAttribute(k_modexp_mixed<RED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)MIX_SMEM);
+        e = cudaFuncSetAttribute(k_modexp_mixed<RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MIX_SMEM);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        int sms = 0, per_sm = 0;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_modexp_mixed<RED>, MIX_TPB, MIX_SMEM)) !=
             cudaSuccess)
             return e;
         grid = sms * (per_sm > 0 ? per_sm : 1);
+        if (dev >= 0 && dev < 64) grids[dev].store(grid, std::memory_order_release);
     }
     const int blocks = std::min(grid, P.total > 0 ? P.total : 1);
     k_modexp_mixed<RED><<<blocks, MIX_TPB, MIX_SMEM, st>>>(P);
