@@ -54,11 +54,14 @@ def test_gpu_reproduces_fixture():
         B = len(rs)
         ctx = mp.MontCtx(mp.to_device(N.reshape(-1)), B, bits, mp.LAYOUT_INSTANCE_MAJOR)
         Y = torch.zeros(B * n, dtype=torch.int32, device="cuda")
-        for red in (mp.RED_TRUNCATED, mp.RED_FULL, mp.RED_CIOS):
-            mp.modexp_consttime(Y, mp.to_device(a.reshape(-1)), mp.to_device(e.reshape(-1)), bits, ctx, 5, red)
+        forms = [(mp.RED_TRUNCATED, mp.ALGO_AUTO), (mp.RED_FULL, mp.ALGO_AUTO), (mp.RED_CIOS, mp.ALGO_AUTO)]
+        if bits > 256:   # the truncated Karatsuba form exists from the 512-bit class up
+            forms.append((mp.RED_TRUNCATED, mp.ALGO_KARATSUBA))
+        for red, algo in forms:
+            mp.modexp_consttime(Y, mp.to_device(a.reshape(-1)), mp.to_device(e.reshape(-1)), bits, ctx, 5, red, algo)
             got = mp.to_host(Y).reshape(B, n)
-            assert [si.to_int(v) for v in got] == [r[5] for r in rs], (bits, red)
-            mp.mont_mul(Y, mp.to_device(a.reshape(-1)), mp.to_device(a.reshape(-1)), ctx, red)
+            assert [si.to_int(v) for v in got] == [r[5] for r in rs], (bits, red, algo)
+            mp.mont_mul(Y, mp.to_device(a.reshape(-1)), mp.to_device(a.reshape(-1)), ctx, red, algo)
             got = mp.to_host(Y).reshape(B, n)
-            assert [si.to_int(v) for v in got] == [r[6] for r in rs], (bits, red)
+            assert [si.to_int(v) for v in got] == [r[6] for r in rs], (bits, red, algo)
         ctx.free()
