@@ -56,9 +56,8 @@ struct Shape {
     static constexpr int OFF_N = 2 * NP;          // modulus
     static constexpr int OFF_NI = 3 * NP;         // N' = (-N)^-1 mod R
     static constexpr int OFF_T = 4 * NP;          // T (2*NP words)
-    static constexpr int OFF_P = 6 * NP;          // slot spills: 2G slots of M+2 words
-    static constexpr int OFF_Z = OFF_P + 2 * G * (M + 2);   // M zero words
-    static constexpr int OFF_XB = OFF_Z + M;      // W_: one byte per thread (predicate exchange)
+    static constexpr int OFF_P = 6 * NP;          // slot spills: 2G slots of M words, then 2G top words
+    static constexpr int OFF_XB = OFF_P + 2 * G * (M + 1);   // W_: one byte per thread (predicate exchange)
     static constexpr int OFF_XW = OFF_XB + (W_ ? (G + 3) / 4 : 0);   // W_: one broadcast word
     static constexpr int WORDS_RAW = OFF_XW + (W_ ? 1 : 0);
     // Instance stride (words), a multiple of 4 (16-byte aligned instances).
@@ -77,8 +76,7 @@ struct Shape {
 template <class S>
 struct Grp {
     uint32_t *sm;   // this instance's shared words
-    uint32_t *pa;   // slot spill area (2G slots of M+2 words)
-    uint32_t *za;   // M zero words
+    uint32_t *pa;   // slot spill area (2G slots of B words, then 2G top words; B = block width)
     int t;          // thread index in the group
     int gbase;      // warp lane of thread 0 of the group (lane mapping)
     MPG_DI uint32_t *X() const { return sm + S::OFF_X; }
@@ -88,7 +86,6 @@ struct Grp {
     MPG_DI uint32_t *NI() const { return sm + S::OFF_NI; }
     MPG_DI uint32_t *T() const { return sm + S::OFF_T; }
     MPG_DI uint32_t *P() const { return pa; }
-    MPG_DI uint32_t *Z() const { return za; }
     // all threads of the group reach this point (and see each other's shared-memory writes)
     MPG_DI void sync() const {
         if constexpr (S::WMAP) MPG_BLOCK_BARRIER();
@@ -196,6 +193,20 @@ MPG_DI void mac_block(uint32_t (&V)[2 * B + 2], const uint32_t *xp, const uint32
     acc_add<B>(V, P);
 }
 
+// mac_block with the product dropped when !live (the Y operand masked to zero), so that
+// threads with fewer block products run the same instructions
+template <int B>
+MPG_DI void mac_block_live(uint32_t (&V)[2 * B + 2], const uint32_t *xp, const uint32_t *yp, bool live) {
+    uint32_t x[B], y[B], P[2 * B];
+    lds<B>(x, xp);
+    lds<B>(y, yp);
+    const uint32_t m = live ? 0xffffffffu : 0u;
+#pragma unroll
+    for (int j = 0; j < B; ++j) y[j] &= m;
+    block_mul<B>(P, x, y);
+    acc_add<B>(V, P);
+}
+
 // V += X_{u(j)} * Y_{v(j)} for j = 0 .. cnt-1 (B-word blocks; uv(j, u, v) gives the pair), with
 // the operands of step j+1 loaded from shared memory while step j multiplies (two register
 // buffers, the loop unrolled by two so they alternate without moves). at(j) runs after step j.
@@ -260,16 +271,28 @@ struct NoXform {
     MPG_DI void operator()(int, uint32_t (&)[A]) const {}
 };
 
+// Spill area of slot s for B-word blocks: words B .. 2B-1 of the slot sum at P + s*B, word 2B
+// at P + 2G*B + s. A slot sum stays below W^(2B+1) (at most 2(2G+1) block products of B x B
+// words, or a doubled and offset square sum), so its word 2B+1 is zero and B+1 spill words hold
+// the rest of it.
+struct Spill {
+    uint32_t *m;   // B words
+    uint32_t *t;   // 1 word
+};
+template <class S, int B>
+MPG_DI Spill spill_of(const Grp<S> &g, int s) {
+    return Spill{g.P() + s * B, g.P() + 2 * S::G * B + s};
+}
+
 // complete slot s: low B words to its output position, the rest to its spill area
 template <int B>
-MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
-    uint32_t lo[B], hi[B + 2];
+MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, Spill sp) {
+    uint32_t lo[B], hi[B];
 #pragma unroll
-    for (int j = 0; j < B; ++j) lo[j] = V[j];
-#pragma unroll
-    for (int j = 0; j < B + 2; ++j) hi[j] = V[B + j];
+    for (int j = 0; j < B; ++j) { lo[j] = V[j]; hi[j] = V[B + j]; }
     sts<B>(out_lo, lo);
-    sts<B + 2>(spill, hi);
+    sts<B>(sp.m, hi);
+    *sp.t = V[2 * B];
     zero<2 * B + 2>(V);
 }
 
@@ -278,27 +301,29 @@ MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
 // the first slot is complete and recovers the second slot at the end as the final sum
 // minus the parked one (unpark_sub), so the loop body never clears registers.
 template <int B>
-MPG_DI void park(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *spill) {
-    uint32_t lo[B], hi[B + 2];
+MPG_DI void park(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, Spill sp) {
+    uint32_t lo[B], hi[B];
 #pragma unroll
-    for (int j = 0; j < B; ++j) lo[j] = V[j];
-#pragma unroll
-    for (int j = 0; j < B + 2; ++j) hi[j] = V[B + j];
+    for (int j = 0; j < B; ++j) { lo[j] = V[j]; hi[j] = V[B + j]; }
     sts<B>(out_lo, lo);
-    sts<B + 2>(spill, hi);
+    sts<B>(sp.m, hi);
+    *sp.t = V[2 * B];
 }
 
 // V -= the sum parked at out_lo / spill (exact: V holds the parked sum plus more)
 template <int B>
-MPG_DI void unpark_sub(uint32_t (&V)[2 * B + 2], const uint32_t *out_lo, const uint32_t *spill) {
-    uint32_t lo[B], hi[B + 2];
+MPG_DI void unpark_sub(uint32_t (&V)[2 * B + 2], const uint32_t *out_lo, Spill sp) {
+    uint32_t lo[B], hi[B];
     lds<B>(lo, out_lo);
-    lds<B + 2>(hi, spill);
+    lds<B>(hi, sp.m);
+    const uint32_t top = *sp.t;
     sub_cc(V[0], lo[0]);
 #pragma unroll
     for (int j = 1; j < B; ++j) subc_cc(V[j], lo[j]);
 #pragma unroll
-    for (int j = 0; j < B + 2; ++j) subc_cc(V[B + j], hi[j]);
+    for (int j = 0; j < B; ++j) subc_cc(V[B + j], hi[j]);
+    subc_cc(V[2 * B], top);
+    subc_cc(V[2 * B + 1], 0u);
 }
 
 // overflow words of the predecessor slot, passed between lanes with shuffles
@@ -331,7 +356,6 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
     constexpr int G = S::G;
     constexpr int SP = B + 2;
     constexpr int NSLOT = 2 * G;
-    uint32_t *Pm = g.P();
     uint32_t lo[2][B];
     uint32_t top = 0u;   // words at and above the last slot (owner lane only)
 
@@ -339,22 +363,24 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int s = slot_of<G, PAT>(g.t, k);
+        const Spill sp = spill_of<S, B>(g, s);
         uint32_t V[2 * B + 2];
         {
-            uint32_t l[B], h[SP];
+            uint32_t l[B], h[B];
             lds<B>(l, OUT + s * B);
-            lds<SP>(h, Pm + s * SP);
+            lds<B>(h, sp.m);
 #pragma unroll
-            for (int j = 0; j < B; ++j) V[j] = l[j];
-#pragma unroll
-            for (int j = 0; j < SP; ++j) V[B + j] = h[j];
+            for (int j = 0; j < B; ++j) { V[j] = l[j]; V[B + j] = h[j]; }
+            V[2 * B] = *sp.t;
+            V[2 * B + 1] = 0u;
         }
-        if constexpr (XF::active) {
+        if constexpr (XF::active) {   // the rewritten sum stays below W^(2B+1) (see spill_of)
             xf(s, V);
-            uint32_t h[SP];
+            uint32_t h[B];
 #pragma unroll
-            for (int j = 0; j < SP; ++j) h[j] = V[B + j];
-            sts<SP>(Pm + s * SP, h);
+            for (int j = 0; j < B; ++j) h[j] = V[B + j];
+            sts<B>(sp.m, h);
+            *sp.t = V[2 * B];
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) lo[k][j] = V[j];
@@ -371,7 +397,13 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
 #pragma unroll
             for (int j = 0; j < SP; ++j) x[j] = in0[j];
         } else {
-            lds<SP>(x, Pm + (s - 1) * SP);
+            const Spill pp = spill_of<S, B>(g, s - 1);
+            uint32_t h[B];
+            lds<B>(h, pp.m);
+#pragma unroll
+            for (int j = 0; j < B; ++j) x[j] = h[j];
+            x[B] = *pp.t;
+            x[B + 1] = 0u;
         }
         add_cc(x[0], lo[k][0]);
 #pragma unroll
@@ -392,16 +424,17 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
         g.sync();
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int s = slot_of<G, PAT>(g.t, k);
-            Pm[s * SP] = ov[k][0];
-            Pm[s * SP + 1] = ov[k][1];
+            uint32_t *m = spill_of<S, B>(g, slot_of<G, PAT>(g.t, k)).m;
+            m[0] = ov[k][0];
+            m[1] = ov[k][1];
         }
         g.sync();
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int s = slot_of<G, PAT>(g.t, k);
-            oin[k][0] = s ? Pm[(s - 1) * SP] : 0u;
-            oin[k][1] = s ? Pm[(s - 1) * SP + 1] : 0u;
+            const uint32_t *m = spill_of<S, B>(g, s > 0 ? s - 1 : 0).m;
+            oin[k][0] = s ? m[0] : 0u;
+            oin[k][1] = s ? m[1] : 0u;
         }
     }
     uint32_t cgen[2], cprop[2];
@@ -451,7 +484,7 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
         MPG_BLOCK_LOOP
         for (int j = 0; j <= t; ++j) mac_block<M>(V, X + j * M, Y + (t - j) * M);
-        flush<M>(V, T + t * M, g.P() + t * (M + 2));
+        flush<M>(V, T + t * M, spill_of<S, M>(g, t));
         MPG_BLOCK_LOOP
         for (int j = t + 1; j < G; ++j) mac_block<M>(V, X + j * M, Y + (t - j + G) * M);
     } else {
@@ -459,11 +492,11 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
         for (int j = 0; j < G; ++j) {
             const int v = (t - j) & (G - 1);
             mac_block<M>(V, X + j * M, Y + v * M);
-            if (j == t) park<M>(V, T + t * M, g.P() + t * (M + 2));
+            if (j == t) park<M>(V, T + t * M, spill_of<S, M>(g, t));
         }
-        unpark_sub<M>(V, T + t * M, g.P() + t * (M + 2));
+        unpark_sub<M>(V, T + t * M, spill_of<S, M>(g, t));
     }
-    park<M>(V, T + (G + t) * M, g.P() + (G + t) * (M + 2));
+    park<M>(V, T + (G + t) * M, spill_of<S, M>(g, G + t));
     g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
@@ -507,7 +540,7 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     if constexpr (S::WMAP) {   // t is uniform across the warp: exact pair counts, no dummy blocks
         MPG_BLOCK_LOOP
         for (int j = 0; j < nA; ++j) mac_block<M>(V, X + j * M, X + (g.t - j) * M);
-        flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+        flush<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
         MPG_BLOCK_LOOP
         for (int j = 0; j < nB; ++j) {
             const int u = g.t + 1 + j;
@@ -516,17 +549,17 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     } else {
         MPG_BLOCK_LOOP
         for (int j = 0; j < K; ++j) {
-            if (j == nA) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+            if (j == nA) park<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
             int u, v;
             if (j < nA) { u = j; v = g.t - j; }
             else { u = g.t + 1 + (j - nA); v = G + g.t - u; }
             const bool live = j < nA + nB;
-            mac_block<M>(V, X + (live ? u : 0) * M, live ? X + v * M : g.Z());
+            mac_block_live<M>(V, X + (live ? u : 0) * M, X + (live ? v : 0) * M, live);
         }
-        if (nA == K) park<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
-        unpark_sub<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+        if (nA == K) park<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
+        unpark_sub<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
     }
-    park<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
+    park<M>(V, T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
     uint32_t x[M], P[2 * M];
     lds<M>(x, X + g.t * M);
     g.sync();                                   // all reads of X are done
@@ -550,7 +583,7 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
         const auto none = [](int) {};
         mac_loop_pipelined<H>(V, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; }, none);
-        flush<H>(V, Q + t * H, g.P() + t * (H + 2));
+        flush<H>(V, Q + t * H, spill_of<S, H>(g, t));
         mac_loop_pipelined<H>(V, X, Y, 2 * G - t, [&](int k, int &u, int &v) { u = k; v = 2 * G - t - 1 - k; },
                               none);
     } else {
@@ -558,7 +591,7 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
             if (j <= t) { u = j; v = t - j; }
             else { u = j - t - 1; v = 2 * G - j; }
         };
-        const auto at = [&](int j) { if (j == t) park<H>(V, Q + t * H, g.P() + t * (H + 2)); };
+        const auto at = [&](int j) { if (j == t) park<H>(V, Q + t * H, spill_of<S, H>(g, t)); };
         if constexpr (PIPELINE_HALF_BLOCKS<S>) {
             mac_loop_pipelined<H>(V, X, Y, 2 * G + 1, uv, at);
         } else {
@@ -570,9 +603,9 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
                 at(j);
             }
         }
-        unpark_sub<H>(V, Q + t * H, g.P() + t * (H + 2));
+        unpark_sub<H>(V, Q + t * H, spill_of<S, H>(g, t));
     }
-    park<H>(V, Q + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
+    park<H>(V, Q + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
     g.sync();
     uint32_t in0[H + 2];
     zero<H + 2>(in0);
@@ -675,7 +708,7 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
         const auto none = [](int) {};
         mac_loop_pipelined<H>(V, Qs, Ns, nA, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; },
                               none);
-        flush<H>(V, C + t * H, g.P() + t * (H + 2));
+        flush<H>(V, C + t * H, spill_of<S, H>(g, t));
         if (t > 0)   // slot B of thread t has t products (none for thread 0)
             mac_loop_pipelined<H>(V, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; },
                                   none);
@@ -684,7 +717,7 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
             if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
             else { u = j + 1; v = 4 * G - 2 - t - j; }
         };
-        const auto at = [&](int j) { if (j == nA - 1) park<H>(V, C + t * H, g.P() + t * (H + 2)); };
+        const auto at = [&](int j) { if (j == nA - 1) park<H>(V, C + t * H, spill_of<S, H>(g, t)); };
         if constexpr (PIPELINE_HALF_BLOCKS<S>) {
             mac_loop_pipelined<H>(V, Qs, Ns, 2 * G - 1, uv, at);
         } else {
@@ -696,9 +729,9 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
                 at(j);
             }
         }
-        unpark_sub<H>(V, C + t * H, g.P() + t * (H + 2));
+        unpark_sub<H>(V, C + t * H, spill_of<S, H>(g, t));
     }
-    park<H>(V, C + (2 * G - 1 - t) * H, g.P() + (2 * G - 1 - t) * (H + 2));
+    park<H>(V, C + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
     if constexpr (S::WMAP) {
         // thread 0 (owner of slot 0, the only one that needs the sum) adds the parked Z's
         g.sync();
@@ -771,11 +804,11 @@ MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *N
         mac_block<M>(V, Qs + j * M, Ns + v * M);
         if (j == g.t) {   // add T's words of this slot, then store over them
             addT(g.t, V);
-            flush<M>(V, T + g.t * M, g.P() + g.t * (M + 2));
+            flush<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
         }
     }
     addT(G + g.t, V);
-    flush<M>(V, T + (G + g.t) * M, g.P() + (G + g.t) * (M + 2));
+    flush<M>(V, T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
     g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);

@@ -69,8 +69,7 @@ struct KaraLayout {
     static constexpr int OFF_D1 = 10 * h;      // D1, then D1 - D0 - D2 (2h)
     static constexpr int OFF_SQ = 12 * h;      // block squares of a half product (2h)
     static constexpr int OFF_P = 14 * h;       // slot spills of the half products
-    static constexpr int OFF_Z = OFF_P + 2 * HS::G * (HS::M + 2);
-    static constexpr int WORDS = (OFF_Z + HS::M + 3) & ~3;
+    static constexpr int WORDS = (OFF_P + 2 * HS::G * (HS::M + 1) + 3) & ~3;
 };
 
 template <class F, class HS, int TPB>
@@ -82,17 +81,12 @@ __global__ void __launch_bounds__(TPB) k_kara(KArgs A) {
     Grp<HS> g;
     g.sm = sm;
     g.pa = sm + L::OFF_P;
-    g.za = sm + L::OFF_Z;
     g.t = threadIdx.x % F::G;
     g.gbase = (threadIdx.x & 31) & ~(F::G - 1);
     const size_t k = (size_t)blockIdx.x * (TPB / F::G) + threadIdx.x / F::G;
     const bool valid = k < A.batch;
     uint32_t *a = sm + L::OFF_A, *b = sm + L::OFF_B, *sa = sm + L::OFF_SA, *sb = sm + L::OFF_SB;
     uint32_t *D = sm + L::OFF_D, *D1 = sm + L::OFF_D1, *SQ = sm + L::OFF_SQ;
-    if (g.t == 0) {
-#pragma unroll
-        for (int j = 0; j < MH; ++j) g.za[j] = 0u;
-    }
     {
         uint32_t x[F::M];
         gload<F::M>(x, A.a, A.layout, k, valid, g.t * F::M, A.n, A.batch);
@@ -183,8 +177,7 @@ struct Kara2Layout {
     static constexpr int OFF_ID1 = OFF_SY + q;      // inner D1 (2q)
     static constexpr int OFF_SQ = OFF_ID1 + 2 * q;  // inner block squares (2q)
     static constexpr int OFF_P = OFF_SQ + 2 * q;    // slot spills of the quarter products
-    static constexpr int OFF_Z = OFF_P + 2 * QS::G * (QS::M + 2);
-    static constexpr int WORDS = (OFF_Z + QS::M + 3) & ~3;
+    static constexpr int WORDS = (OFF_P + 2 * QS::G * (QS::M + 1) + 3) & ~3;
 };
 
 template <class QS, int TPB>
@@ -196,7 +189,6 @@ __global__ void __launch_bounds__(TPB) k_kara2(KArgs A) {
     Grp<QS> g;
     g.sm = sm;
     g.pa = sm + L::OFF_P;
-    g.za = sm + L::OFF_Z;
     g.t = threadIdx.x % G;
     g.gbase = (threadIdx.x & 31) & ~(G - 1);
     const size_t k = (size_t)blockIdx.x * (TPB / G) + threadIdx.x / G;
@@ -204,10 +196,6 @@ __global__ void __launch_bounds__(TPB) k_kara2(KArgs A) {
     uint32_t *a = sm + L::OFF_A, *b = sm + L::OFF_B, *sa = sm + L::OFF_SA, *sb = sm + L::OFF_SB;
     uint32_t *D = sm + L::OFF_D, *D1 = sm + L::OFF_D1;
     uint32_t *sx = sm + L::OFF_SX, *sy = sm + L::OFF_SY, *id1 = sm + L::OFF_ID1, *sq = sm + L::OFF_SQ;
-    if (g.t == 0) {
-#pragma unroll
-        for (int j = 0; j < MQ; ++j) g.za[j] = 0u;
-    }
     {
         uint32_t x[MF];
         gload<MF>(x, A.a, A.layout, k, valid, g.t * MF, A.n, A.batch);

@@ -105,7 +105,6 @@ MPG_DI Grp<S> make_group(uint32_t *smem) {
     Grp<S> g;
     g.sm = smem + local_instance<S>() * S::WORDS;
     g.pa = g.sm + S::OFF_P;
-    g.za = g.sm + S::OFF_Z;
     if constexpr (S::WMAP) {
         g.t = (int)(threadIdx.x >> 5);
         g.gbase = 0;
@@ -121,14 +120,6 @@ template <class S, int TPB>
 MPG_DI size_t global_instance() {
     static_assert(!S::WMAP || TPB == 32 * S::G, "warp mapping: one block = G warps");
     return (size_t)blockIdx.x * (TPB / S::G) + local_instance<S>();
-}
-
-template <class S>
-MPG_DI void init_zero_block(const Grp<S> &g) {
-    if (g.t == 0) {
-#pragma unroll
-        for (int j = 0; j < S::M; ++j) g.Z()[j] = 0u;
-    }
 }
 
 // load M words per thread of an API operand into shared memory
@@ -167,7 +158,6 @@ __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mul(KArgs A)
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = global_instance<S, TPB>();
     const bool valid = k < A.batch;
-    init_zero_block<S>(g);
     load_api<S>(g, g.X(), A.a, A, k, valid);
     if (!A.square) load_api<S>(g, g.Y(), A.b, A, k, valid);
     g.sync();
@@ -187,7 +177,6 @@ __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mont(KArgs A
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = global_instance<S, TPB>();
     const bool valid = k < A.batch;
-    init_zero_block<S>(g);
     load_ctx<S>(g, g.N(), A.N, A, k, valid);
     load_ctx<S>(g, g.NI(), A.NI, A, k, valid);
     load_api<S>(g, g.X(), A.a, A, k, valid);
@@ -278,7 +267,6 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
         }
     };
 
-    init_zero_block<S>(g);
     load_ctx<S>(g, g.N(), A.N, A, kc, valid);
     load_ctx<S>(g, g.NI(), A.NI, A, kc, valid);
     // The products of the job, in order, run from ONE call site (one copy of the

@@ -45,9 +45,8 @@ struct KShape {
     static constexpr int OFF_SN = 6 * NP;         // s_N = N_l + N_h mod W^h
     static constexpr int OFF_SNI = OFF_SN + h;    // s_N' = N'_l + N'_h mod W^h
     static constexpr int OFF_A = OFF_SNI + h;     // scratch (4h words), see tk_product
-    static constexpr int OFF_P = OFF_A + 4 * h;   // slot spills: 2G slots of MH+2 words
-    static constexpr int OFF_Z = OFF_P + 2 * G * (MH + 2);   // M zero words
-    static constexpr int OFF_CN = OFF_Z + M;      // c_N, the carry of N_l + N_h
+    static constexpr int OFF_P = OFF_A + 4 * h;   // slot spills: 2G slots of MH words + 2G top words
+    static constexpr int OFF_CN = OFF_P + 2 * G * (MH + 1);   // c_N, the carry of N_l + N_h
     static constexpr int WORDS_RAW = OFF_CN + 1;
     static constexpr int BANK_RES = G < 16 ? 2 * G : 16;   // instance stride as for Shape
     static constexpr int WORDS_A = (WORDS_RAW + 3) & ~3;
@@ -101,7 +100,6 @@ MPG_DI Grp<typename S::HS> half_view(const Grp<S> &g) {
     Grp<typename S::HS> gh;
     gh.sm = g.sm;
     gh.pa = g.pa;
-    gh.za = g.za;
     gh.t = g.t;
     gh.gbase = g.gbase;
     return gh;
