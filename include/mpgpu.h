@@ -86,7 +86,8 @@ int mp_convert(uint32_t *dst, mp_layout dst_layout, const uint32_t *src, mp_layo
  * algo: SCHOOLBOOK, KARATSUBA (one level, Sec. 3: three half-size products; sizes
  * above 512 bits, else MP_ERR_UNIMPLEMENTED), KARATSUBA2 (two levels, the 9 quarter
  * products of Sec. 3 applied twice; 4097..4608-bit and 3073..4096-bit sizes only, else
- * MP_ERR_UNIMPLEMENTED) or AUTO (Karatsuba above 4096 bits).
+ * MP_ERR_UNIMPLEMENTED) or AUTO (schoolbook, the faster form on GB300 at every size, unless
+ * mp_tune_set sets a Karatsuba switch-over for the class).
  * c must not overlap a or b.
  */
 int mp_mul(uint32_t *c, const uint32_t *a, const uint32_t *b, size_t batch, uint32_t bits,

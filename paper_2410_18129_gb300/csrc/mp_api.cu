@@ -34,9 +34,11 @@ using namespace mpg;
 
 static constexpr uint32_t MAX_NP = 144;   // largest padded size: 8 threads x 18 words
 static constexpr uint32_t MAX_BITS = 32 * MAX_NP;
-// MP_ALGO_AUTO switch-over for products: measured on GB300, schoolbook wins at 4096 bits
-// (266 vs 216 M mul/s) and Karatsuba above it (4108/4154 bits: 214 vs 195 M mul/s)
-static constexpr uint32_t KARATSUBA_FROM_BITS = 4097;
+// MP_ALGO_AUTO switch-over for products: measured on GB300, schoolbook wins at every size
+// (M products/s, schoolbook vs one Karatsuba level: 4096 bits mul 263 / 205, sqr 397 / 224;
+// 4108 bits 221 / 218, 348 / 285; 4154 bits 239 / 220, 355 / 288), so AUTO never picks Karatsuba
+// unless mp_tune_set sets a switch-over
+static constexpr uint32_t KARATSUBA_FROM_BITS = 0xffffffffu;
 
 // Size classes: one per padded size NP. Each class has one or more compiled group
 // shapes (threads per instance x words per thread); the first is the default and

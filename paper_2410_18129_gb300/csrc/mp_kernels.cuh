@@ -138,15 +138,16 @@ MPG_DI void load_ctx(const Grp<S> &g, uint32_t *dst, const uint32_t *src, const 
 }
 
 // Blocks per SM that the shared memory of a shape allows (228 KB per SM, 1 KB of it reserved per
-// block), but never so many that a thread gets fewer than 64 registers (200 for operands of more
-// than 16 words per thread, whose block products measured 29 % slower at 140 registers than at
-// about 220). The kernels declare it as their minimum blocks per SM, so the compiler may use every
+// block), but never so many that a thread gets fewer than 64 registers. Montgomery kernels (MONT)
+// of shapes with more than 16 words per thread keep 200: their exponentiation measured 29 % slower
+// at 140 registers than at about 220, while their plain products run faster at the higher
+// occupancy. The kernels declare it as their minimum blocks per SM, so the compiler may use every
 // register that this occupancy leaves.
-template <class S, int TPB>
+template <class S, int TPB, bool MONT = true>
 constexpr int blocks_per_sm() {
     constexpr long smem = (long)(TPB / S::G) * S::WORDS * 4 + 1024;
     constexpr long by_smem = 233472L / smem;
-    constexpr long min_regs = S::M > 16 ? 200L : 64L;
+    constexpr long min_regs = (MONT && S::M > 16) ? 200L : 64L;
     constexpr long by_regs = 65536L / (TPB * min_regs);
     constexpr long b = by_smem < by_regs ? by_smem : by_regs;
     return b < 1 ? 1 : (int)b;
@@ -155,7 +156,7 @@ constexpr int blocks_per_sm() {
 // ------------------------------------------------------------------ mp_mul / mp_sqr
 
 template <class S, int TPB>
-__global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_mul(KArgs A) {
+__global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB, false>())) k_mul(KArgs A) {
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = global_instance<S, TPB>();
