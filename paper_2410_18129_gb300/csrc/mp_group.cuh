@@ -7,7 +7,7 @@
 // the same number of block products (balanced even for the triangular low and
 // high halves) and accumulates each slot in registers. When a slot is complete
 // its low B words go straight to the phase's output array and its spill (the
-// words above, B+2 of them) to a small shared area. A carry-resolution pass then
+// words above, B+1 of them) to a small shared area. A carry-resolution pass then
 // adds each predecessor's spill, passes a small overflow word to the successor
 // through a shuffle, and resolves the remaining one-bit carries for the whole
 // group at once with warp ballots (carry-lookahead).
@@ -346,7 +346,7 @@ MPG_DI void pred_overflow(int t, int gbase, const uint32_t (&ovA)[2], const uint
 }
 
 // Turn completed slots (low B words already at OUT[s*B..], spill words at
-// P[s*(B+2)..]) into words OUT[s*B..s*B+B). in0: B+2 words added below slot 0 (a
+// spill_of(s)) into words OUT[s*B..s*B+B). in0: B+2 words added below slot 0 (a
 // carry coming from outside). xf may rewrite a slot sum first (add an addend,
 // double it ...). Returns the low word of everything above the last slot (its own
 // spill and overflow plus the resolved carry).
