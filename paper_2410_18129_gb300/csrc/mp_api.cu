@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -585,7 +586,7 @@ extern "C" int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint3
 static __device__ __align__(256) uint4 g_noalloc_tables[MPGPU_NOALLOC_SCRATCH_BYTES / 16];
 
 static constexpr int NOALLOC_MAX_DEVICES = 64;
-static uint32_t *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+static std::atomic<uint32_t *> g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
 
 // Device address of the array on the current device. In host code the array's
 // name only stands for the device symbol, so the address comes from
@@ -593,15 +594,17 @@ static uint32_t *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the 
 static int noalloc_tables(uint32_t **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MP_ERR_CUDA;
-    if (!g_noalloc_ptr[dev]) {
+    uint32_t *ptr = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!ptr) {   // two threads racing here look up and store the same address
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_tables) != cudaSuccess || !p) {
             cudaGetLastError();
             return MP_ERR_CUDA;
         }
-        g_noalloc_ptr[dev] = reinterpret_cast<uint32_t *>(p);
+        ptr = reinterpret_cast<uint32_t *>(p);
+        g_noalloc_ptr[dev].store(ptr, std::memory_order_release);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = ptr;
     return MP_OK;
 }
 
