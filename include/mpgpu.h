@@ -47,7 +47,7 @@ typedef enum {
     MP_ERR_ALIGN = -4,          /* pointer not 16-byte aligned */
     MP_ERR_CUDA = -5,           /* a CUDA runtime call or kernel launch failed */
     MP_ERR_NOMEM = -6,          /* device allocation failed or workspace too small */
-    MP_ERR_UNIMPLEMENTED = -7,  /* combination not provided by this build */
+    MP_ERR_UNIMPLEMENTED = -7,  /* combination the library does not provide */
     MP_ERR_TIMEOUT = -8         /* a bounded device-side wait gave up (persistent kernels) */
 } mp_status;
 
@@ -66,7 +66,7 @@ typedef struct mont_ctx mont_ctx;
 /* Human-readable text for a status code (static storage). */
 const char *mp_strerror(int status);
 
-/* Largest operand size in bits supported by this build. */
+/* Largest operand size in bits the library supports. */
 uint32_t mp_max_bits(void);
 
 /* Library version string (static storage). */
