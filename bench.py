@@ -638,7 +638,8 @@ def bench_serving(args):
     rates = (1e4, 3e4, 1e5, 3e5, 1e6)
     seconds = 4.0
     cap = 100000 if args.batch == 65536 else args.batch
-    pool = sv.Pool(mp, seed=0, count=4096)
+    pin = si.serving_pool(0, 4096)
+    pool = sv.Pool(mp, pin.sizes, pin.moduli, pin.bases)
     traces = {r: si.poisson_trace(0, r, int(min(r * seconds, cap)), pool.sizes) for r in rates}
     free = torch.cuda.mem_get_info()[0]
     out = {}

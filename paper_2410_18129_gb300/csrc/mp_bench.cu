@@ -156,8 +156,70 @@ __global__ void __launch_bounds__(512) k_bench_wide(int iters, uint32_t seed, ui
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// modes 9-12: block products summed into one running slot sum, as the Montgomery phases do
+// (768 threads per SM, 24 warps):
+//   9: 8x8 blocks, split-column accumulator (Acc3<8>)      10: 4x4 blocks, Acc3<4>
+//  11: 8x8 blocks, block_mul + acc_add into one array      12: 4x4 blocks, block_mul + acc_add
+// 128 multiply-adds (64 partial products) per iteration in every mode.
+template <int MODE>
+__global__ void __launch_bounds__(768, 1) k_bench_acc(int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
+    constexpr int B = (MODE == 9 || MODE == 11) ? 8 : 4;
+    constexpr int REP = 64 / (B * B);
+    uint32_t x[B], y[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) { x[i] = seed * (threadIdx.x + 3 * i + 1); y[i] = seed ^ (i * 0x9e3779b9u + threadIdx.x); }
+    uint32_t fold = 0u;
+    __syncthreads();
+    long long t0 = clock64();
+    if constexpr (MODE == 9 || MODE == 10) {
+        Acc3<B> a;
+        acc3_zero<B>(a);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int r = 0; r < REP; ++r) acc3_mac<B>(a, x, y);
+#pragma unroll
+            for (int i = 0; i < B; ++i) x[i] ^= a.E[i];
+        }
+        uint32_t V[2 * B + 2];
+        acc3_value<B>(V, a);
+#pragma unroll
+        for (int j = 0; j < 2 * B + 2; ++j) fold ^= V[j];
+    } else {
+        uint32_t V[2 * B + 2];
+#pragma unroll
+        for (int j = 0; j < 2 * B + 2; ++j) V[j] = 0u;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int r = 0; r < REP; ++r) {
+                uint32_t P[2 * B];
+                block_mul<B>(P, x, y);
+                acc_add<B>(V, P);
+            }
+#pragma unroll
+            for (int i = 0; i < B; ++i) x[i] ^= V[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * B + 2; ++j) fold ^= V[j];
+    }
+    __syncthreads();
+    long long t1 = clock64();
+#pragma unroll
+    for (int i = 0; i < B; ++i) fold ^= x[i] + y[i];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = fold;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+static void launch_acc(int mode, int sms, int iters, cudaStream_t st, uint32_t *sink, long long *cyc) {
+    switch (mode) {
+        case 9: k_bench_acc<9><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
+        case 10: k_bench_acc<10><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
+        case 11: k_bench_acc<11><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
+        default: k_bench_acc<12><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
+    }
+}
+
 extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream) {
-    if (mode < 0 || mode > 8 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
+    if (mode < 0 || mode > 12 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MP_ERR_CUDA;
@@ -174,6 +236,10 @@ extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double
         k_bench_wide<<<sms, 512, 0, st>>>(1, 12345u, sink, cyc);   // warm-up
         cudaEventRecord(e0, st);
         k_bench_wide<<<sms, 512, 0, st>>>(iters, 12345u, sink, cyc);
+    } else if (mode >= 9) {
+        launch_acc(mode, sms, 1, st, sink, cyc);   // warm-up
+        cudaEventRecord(e0, st);
+        launch_acc(mode, sms, iters, st, sink, cyc);
     } else {
         k_bench<<<sms, threads, 0, st>>>(mode, 1, 12345u, sink, cyc);   // warm-up
         cudaEventRecord(e0, st);
@@ -189,7 +255,7 @@ extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double
         // multiply-adds per thread: every mode is sized to 128 per iteration (mode 6: 256),
         // mode 7 runs on a quarter of the threads
         const double per_thread = (mode == 6 ? 256.0 : mode == 8 ? 200.0 : 128.0) * iters;
-        const double active = mode == 7 ? 256.0 : mode == 8 ? 512.0 : (double)threads;
+        const double active = mode == 7 ? 256.0 : mode == 8 ? 512.0 : mode >= 9 ? 768.0 : (double)threads;
         *per_clk_per_sm = per_thread * active / med;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);

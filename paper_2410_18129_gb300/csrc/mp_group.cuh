@@ -183,37 +183,35 @@ MPG_DI void zero(uint32_t (&x)[K]) {
     for (int k = 0; k < K; ++k) x[k] = 0u;
 }
 
-// V += X_u * Y_v for B-word blocks at p and q
+// a += X_u * Y_v for B-word blocks at p and q
 template <int B>
-MPG_DI void mac_block(uint32_t (&V)[2 * B + 2], const uint32_t *xp, const uint32_t *yp) {
-    uint32_t x[B], y[B], P[2 * B];
+MPG_DI void mac_block(Acc3<B> &a, const uint32_t *xp, const uint32_t *yp) {
+    uint32_t x[B], y[B];
     lds<B>(x, xp);
     lds<B>(y, yp);
-    block_mul<B>(P, x, y);
-    acc_add<B>(V, P);
+    acc3_mac<B>(a, x, y);
 }
 
 // mac_block with the product dropped when !live (the Y operand masked to zero), so that
 // threads with fewer block products run the same instructions
 template <int B>
-MPG_DI void mac_block_live(uint32_t (&V)[2 * B + 2], const uint32_t *xp, const uint32_t *yp, bool live) {
-    uint32_t x[B], y[B], P[2 * B];
+MPG_DI void mac_block_live(Acc3<B> &a, const uint32_t *xp, const uint32_t *yp, bool live) {
+    uint32_t x[B], y[B];
     lds<B>(x, xp);
     lds<B>(y, yp);
     const uint32_t m = live ? 0xffffffffu : 0u;
 #pragma unroll
     for (int j = 0; j < B; ++j) y[j] &= m;
-    block_mul<B>(P, x, y);
-    acc_add<B>(V, P);
+    acc3_mac<B>(a, x, y);
 }
 
-// V += X_{u(j)} * Y_{v(j)} for j = 0 .. cnt-1 (B-word blocks; uv(j, u, v) gives the pair), with
+// a += X_{u(j)} * Y_{v(j)} for j = 0 .. cnt-1 (B-word blocks; uv(j, u, v) gives the pair), with
 // the operands of step j+1 loaded from shared memory while step j multiplies (two register
 // buffers, the loop unrolled by two so they alternate without moves). at(j) runs after step j.
 template <int B, class UV, class AT>
-MPG_DI void mac_loop_pipelined(uint32_t (&V)[2 * B + 2], const uint32_t *X, const uint32_t *Y, int cnt,
+MPG_DI void mac_loop_pipelined(Acc3<B> &V, const uint32_t *X, const uint32_t *Y, int cnt,
                                const UV &uv, const AT &at) {
-    uint32_t xa[B], ya[B], xb[B], yb[B], P[2 * B];
+    uint32_t xa[B], ya[B], xb[B], yb[B];
     int u, v;
     uv(0, u, v);
     lds<B>(xa, X + u * B);
@@ -224,19 +222,16 @@ MPG_DI void mac_loop_pipelined(uint32_t (&V)[2 * B + 2], const uint32_t *X, cons
         uv(j + 1, u, v);
         lds<B>(xb, X + u * B);
         lds<B>(yb, Y + v * B);
-        block_mul<B>(P, xa, ya);
-        acc_add<B>(V, P);
+        acc3_mac<B>(V, xa, ya);
         at(j);
         uv(j + 2 < cnt ? j + 2 : j + 1, u, v);   // the last pair reloads in-range operands
         lds<B>(xa, X + u * B);
         lds<B>(ya, Y + v * B);
-        block_mul<B>(P, xb, yb);
-        acc_add<B>(V, P);
+        acc3_mac<B>(V, xb, yb);
         at(j + 1);
     }
     if (j < cnt) {
-        block_mul<B>(P, xa, ya);
-        acc_add<B>(V, P);
+        acc3_mac<B>(V, xa, ya);
         at(j);
     }
 }
@@ -284,31 +279,38 @@ MPG_DI Spill spill_of(const Grp<S> &g, int s) {
     return Spill{g.P() + s * B, g.P() + 2 * S::G * B + s};
 }
 
-// complete slot s: low B words to its output position, the rest to its spill area
+// store a slot sum: low B words to out_lo, the rest to the slot's spill area
 template <int B>
-MPG_DI void flush(uint32_t (&V)[2 * B + 2], uint32_t *out_lo, Spill sp) {
+MPG_DI void store_slot(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, Spill sp) {
     uint32_t lo[B], hi[B];
 #pragma unroll
     for (int j = 0; j < B; ++j) { lo[j] = V[j]; hi[j] = V[B + j]; }
     sts<B>(out_lo, lo);
     sts<B>(sp.m, hi);
     *sp.t = V[2 * B];
-    zero<2 * B + 2>(V);
 }
 
-// store a slot's running sum without clearing it (low B words to out_lo, the rest to
-// spill). A thread accumulates its two slots in ONE register sum: it parks the sum when
-// the first slot is complete and recovers the second slot at the end as the final sum
-// minus the parked one (unpark_sub), so the loop body never clears registers.
+// store a slot's running sum without clearing it. A thread accumulates its two slots in ONE
+// register sum: it parks the sum when the first slot is complete and recovers the second slot
+// at the end as the final sum minus the parked one (unpark_sub), so the loop body never clears
+// registers.
 template <int B>
-MPG_DI void park(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, Spill sp) {
-    uint32_t lo[B], hi[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j) { lo[j] = V[j]; hi[j] = V[B + j]; }
-    sts<B>(out_lo, lo);
-    sts<B>(sp.m, hi);
-    *sp.t = V[2 * B];
+MPG_DI void park(const Acc3<B> &a, uint32_t *out_lo, Spill sp) {
+    uint32_t V[2 * B + 2];
+    acc3_value<B>(V, a);
+    store_slot<B>(V, out_lo, sp);
 }
+
+// complete slot s: store it and clear the accumulator
+template <int B>
+MPG_DI void flush(Acc3<B> &a, uint32_t *out_lo, Spill sp) {
+    park<B>(a, out_lo, sp);
+    acc3_zero<B>(a);
+}
+
+// the second slot of a parked sum: V = a - the sum parked at out_lo / spill, stored as slot s2
+template <int B>
+MPG_DI void unpark_store(const Acc3<B> &a, const uint32_t *out_lo, Spill sp, uint32_t *out2, Spill sp2);
 
 // V -= the sum parked at out_lo / spill (exact: V holds the parked sum plus more)
 template <int B>
@@ -324,6 +326,14 @@ MPG_DI void unpark_sub(uint32_t (&V)[2 * B + 2], const uint32_t *out_lo, Spill s
     for (int j = 0; j < B; ++j) subc_cc(V[B + j], hi[j]);
     subc_cc(V[2 * B], top);
     subc_cc(V[2 * B + 1], 0u);
+}
+
+template <int B>
+MPG_DI void unpark_store(const Acc3<B> &a, const uint32_t *out_lo, Spill sp, uint32_t *out2, Spill sp2) {
+    uint32_t V[2 * B + 2];
+    acc3_value<B>(V, a);
+    unpark_sub<B>(V, out_lo, sp);
+    store_slot<B>(V, out2, sp2);
 }
 
 // overflow words of the predecessor slot, passed between lanes with shuffles
@@ -473,13 +483,14 @@ MPG_DI uint32_t resolve(const Grp<S> &g, const uint32_t (&in0)[B + 2], const XF 
 
 // ------------------------------------------------------------------ products
 
-// T = X * Y (2*NP words). Full blocks: thread t owns slots t and G+t and computes
-// X_j * Y_{(t-j) mod G} for j = 0..G-1 (G block products for every thread).
+// Slot sums of T = X * Y (2*NP words), stored unresolved (low words at T, spills in P).
+// Full blocks: thread t owns slots t and G+t and computes X_j * Y_{(t-j) mod G} for
+// j = 0..G-1 (G block products for every thread).
 template <class S>
-MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *T) {
-    constexpr int G = S::G, M = S::M, A = S::A1;
-    uint32_t V[A];
-    zero<A>(V);
+MPG_DI void mul_slots(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *T) {
+    constexpr int G = S::G, M = S::M;
+    Acc3<M> V;
+    acc3_zero<M>(V);
     const int t = g.t;
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
         MPG_BLOCK_LOOP
@@ -487,6 +498,7 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
         flush<M>(V, T + t * M, spill_of<S, M>(g, t));
         MPG_BLOCK_LOOP
         for (int j = t + 1; j < G; ++j) mac_block<M>(V, X + j * M, Y + (t - j + G) * M);
+        park<M>(V, T + (G + t) * M, spill_of<S, M>(g, G + t));
     } else {
         MPG_BLOCK_LOOP
         for (int j = 0; j < G; ++j) {
@@ -494,9 +506,15 @@ MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uin
             mac_block<M>(V, X + j * M, Y + v * M);
             if (j == t) park<M>(V, T + t * M, spill_of<S, M>(g, t));
         }
-        unpark_sub<M>(V, T + t * M, spill_of<S, M>(g, t));
+        unpark_store<M>(V, T + t * M, spill_of<S, M>(g, t), T + (G + t) * M, spill_of<S, M>(g, G + t));
     }
-    park<M>(V, T + (G + t) * M, spill_of<S, M>(g, G + t));
+}
+
+// T = X * Y (2*NP words)
+template <class S>
+MPG_DI void phase_mul(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *T) {
+    constexpr int M = S::M;
+    mul_slots<S>(g, X, Y, T);
     g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
@@ -525,18 +543,16 @@ struct SqrXform {
     }
 };
 
-// T = X^2 (Alg. 2 structure): twice the cross products X_u X_v, u < v, plus the
-// squares of the G blocks. Thread t owns slots t and G+t (pairs u < v with
-// u + v = t and G + t). The block squares (one per thread) are formed after the
-// cross products and parked side by side in D (2*NP words; D may overlap X).
+// Slot sums of the cross products of X^2 (Alg. 2 structure): X_u X_v, u < v, not yet
+// doubled. Thread t owns slots t and G+t (pairs u < v with u + v = t and G + t).
 template <class S>
-MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t *T) {
-    constexpr int G = S::G, M = S::M, A = S::A1;
+MPG_DI void sqr_slots(const Grp<S> &g, const uint32_t *X, uint32_t *T) {
+    constexpr int G = S::G, M = S::M;
     const int nA = (g.t + 1) >> 1;              // pairs u < v with u + v = t
     const int nB = ((G - g.t + 1) >> 1) - 1;    // pairs with u + v = G + t
     constexpr int K = G / 2;                    // max of nA + nB over the group
-    uint32_t V[A];
-    zero<A>(V);
+    Acc3<M> V;
+    acc3_zero<M>(V);
     if constexpr (S::WMAP) {   // t is uniform across the warp: exact pair counts, no dummy blocks
         MPG_BLOCK_LOOP
         for (int j = 0; j < nA; ++j) mac_block<M>(V, X + j * M, X + (g.t - j) * M);
@@ -546,6 +562,7 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
             const int u = g.t + 1 + j;
             mac_block<M>(V, X + u * M, X + (G + g.t - u) * M);
         }
+        park<M>(V, T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
     } else {
         MPG_BLOCK_LOOP
         for (int j = 0; j < K; ++j) {
@@ -557,9 +574,17 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
             mac_block_live<M>(V, X + (live ? u : 0) * M, X + (live ? v : 0) * M, live);
         }
         if (nA == K) park<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
-        unpark_sub<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
+        unpark_store<M>(V, T + g.t * M, spill_of<S, M>(g, g.t), T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
     }
-    park<M>(V, T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
+}
+
+// T = X^2: twice the cross products plus the squares of the G blocks. The block squares
+// (one per thread) are formed after the cross products and parked side by side in D
+// (2*NP words; D may overlap X); the resolve doubles each slot sum and adds them.
+template <class S>
+MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t *T) {
+    constexpr int M = S::M;
+    sqr_slots<S>(g, X, T);
     uint32_t x[M], P[2 * M];
     lds<M>(x, X + g.t * M);
     g.sync();                                   // all reads of X are done
@@ -571,14 +596,14 @@ MPG_DI void phase_sqr(const Grp<S> &g, const uint32_t *X, uint32_t *D, uint32_t 
     resolve<S, M, PAT_SEQ>(g, in0, SqrXform<S>{D}, T);
 }
 
-// Q = (X * Y) mod W^NP with half blocks (H words, 2G of them). Thread t owns
+// Slot sums of Q = (X * Y) mod W^NP with half blocks (H words, 2G of them). Thread t owns
 // slots t and 2G-1-t: t+1 and 2G-t block products, 2G+1 for every thread.
 template <class S>
-MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
+MPG_DI void mullo_slots(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
     static_assert(S::MONT_OK, "Montgomery needs an even M >= 4");
-    constexpr int G = S::G, H = S::H, A = S::A2;
-    uint32_t V[A];
-    zero<A>(V);
+    constexpr int G = S::G, H = S::H;
+    Acc3<H> V;
+    acc3_zero<H>(V);
     const int t = g.t;
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
         const auto none = [](int) {};
@@ -586,6 +611,7 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
         flush<H>(V, Q + t * H, spill_of<S, H>(g, t));
         mac_loop_pipelined<H>(V, X, Y, 2 * G - t, [&](int k, int &u, int &v) { u = k; v = 2 * G - t - 1 - k; },
                               none);
+        park<H>(V, Q + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
     } else {
         const auto uv = [&](int j, int &u, int &v) {
             if (j <= t) { u = j; v = t - j; }
@@ -603,9 +629,16 @@ MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, u
                 at(j);
             }
         }
-        unpark_sub<H>(V, Q + t * H, spill_of<S, H>(g, t));
+        unpark_store<H>(V, Q + t * H, spill_of<S, H>(g, t), Q + (2 * G - 1 - t) * H,
+                        spill_of<S, H>(g, 2 * G - 1 - t));
     }
-    park<H>(V, Q + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
+}
+
+// Q = (X * Y) mod W^NP
+template <class S>
+MPG_DI void phase_mullo(const Grp<S> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
+    constexpr int H = S::H;
+    mullo_slots<S>(g, X, Y, Q);
     g.sync();
     uint32_t in0[H + 2];
     zero<H + 2>(in0);
@@ -672,12 +705,13 @@ MPG_DI void tri_mac(uint32_t (&Z)[H + 3], const uint32_t *xp, const uint32_t *yp
 //     known: it is L = ((-T) mod R)[NP-1] (Thm. 1: T + qN = 0 mod R). Hence the
 //     carry out of column NP-1 is floor(Z / W) plus one exactly when L < Z[0].
 //
-// mulhi_sums forms the parts that do not depend on T: the output slots (parked, not yet
-// resolved) and the group sum Z (lane mapping: every thread holds it; warp mapping:
-// thread 0 does).
+// mulhi_slots forms the parts that do not depend on T: the output slots (parked, not yet
+// resolved) and this thread's share Z of the boundary sum (warp mapping: also parked in T's
+// low half, dead once q is formed); mulhi_sums adds the shares over the group (lane mapping:
+// every thread holds the sum; warp mapping: thread 0 does).
 template <class S>
-MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *C, uint32_t (&Z)[S::H + 3]) {
-    constexpr int G = S::G, H = S::H, A = S::A2, NP = S::NP;
+MPG_DI void mulhi_slots(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *C, uint32_t (&Z)[S::H + 3]) {
+    constexpr int G = S::G, H = S::H, NP = S::NP;
     // column NP-1 and the hi halves that reach it: thread t takes diagonal blocks u = 2t, 2t+1
     zero<H + 3>(Z);
 #pragma unroll
@@ -700,8 +734,8 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
         for (int k = 0; k < H + 3; ++k) zs[k] = Z[k];
     }
     // output slots: A = t (absolute 2G+t), B = 2G-1-t (absolute 4G-1-t)
-    uint32_t V[A];
-    zero<A>(V);
+    Acc3<H> V;
+    acc3_zero<H>(V);
     const int t = g.t;
     const int nA = 2 * G - 1 - t;
     if constexpr (S::WMAP) {   // t is uniform across the warp: one loop per slot
@@ -712,6 +746,7 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
         if (t > 0)   // slot B of thread t has t products (none for thread 0)
             mac_loop_pipelined<H>(V, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; },
                                   none);
+        park<H>(V, C + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
     } else {
         const auto uv = [&](int j, int &u, int &v) {
             if (j < nA) { u = t + 1 + j; v = 2 * G + t - u; }
@@ -729,9 +764,16 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
                 at(j);
             }
         }
-        unpark_sub<H>(V, C + t * H, spill_of<S, H>(g, t));
+        unpark_store<H>(V, C + t * H, spill_of<S, H>(g, t), C + (2 * G - 1 - t) * H,
+                        spill_of<S, H>(g, 2 * G - 1 - t));
     }
-    park<H>(V, C + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
+}
+
+template <class S>
+MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *C, uint32_t (&Z)[S::H + 3]) {
+    constexpr int G = S::G, H = S::H;
+    const int t = g.t;
+    mulhi_slots<S>(g, Qs, Ns, C, Z);
     if constexpr (S::WMAP) {
         // thread 0 (owner of slot 0, the only one that needs the sum) adds the parked Z's
         g.sync();
@@ -755,12 +797,14 @@ MPG_DI void mulhi_sums(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, 
     }
 }
 
-template <class S>
-MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, const uint32_t *T,
-                            uint32_t c_add, uint32_t low_zero, uint32_t *C) {
+// C = floor(T/R) + floor(q*N/R) + c_add from the stored slots of the high half and the group
+// sum Z (word 0 at column NP-1); returns the carry out of C
+// (xf: the transform that adds T's high words to the slot sums, unless the slots already
+// hold them)
+template <class S, class XF>
+MPG_DI uint32_t mulhi_resolve(const Grp<S> &g, const uint32_t (&Z)[S::H + 3], const uint32_t *T, uint32_t c_add,
+                              uint32_t low_zero, uint32_t *C, const XF &xf) {
     constexpr int H = S::H, NP = S::NP;
-    uint32_t Z[H + 3];
-    mulhi_sums<S>(g, Qs, Ns, C, Z);
     // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
     const uint32_t L = ~T[NP - 1] + low_zero;
     const uint32_t extra = (uint32_t)(((uint64_t)L - (uint64_t)Z[0]) >> 63);   // [L < Z[0]]
@@ -768,8 +812,17 @@ MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t 
 #pragma unroll
     for (int j = 0; j < H + 2; ++j) in0[j] = Z[1 + j];
     add_word<H + 2>(in0, extra + c_add);
+    return resolve<S, H, PAT_ZIGZAG>(g, in0, xf, C);
+}
+
+template <class S>
+MPG_DI uint32_t phase_mulhi(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, const uint32_t *T,
+                            uint32_t c_add, uint32_t low_zero, uint32_t *C) {
+    constexpr int H = S::H;
+    uint32_t Z[H + 3];
+    mulhi_sums<S>(g, Qs, Ns, C, Z);
     g.sync();
-    return resolve<S, H, PAT_ZIGZAG>(g, in0, AddendXform<H>{T + NP}, C);
+    return mulhi_resolve<S>(g, Z, T, c_add, low_zero, C, AddendXform<H>{T + S::NP});
 }
 
 // Column estimate of floor(X*Y / W^(NP-1)) from the same partial products (the truncated
@@ -790,25 +843,40 @@ MPG_DI uint32_t phase_mulhi_est(const Grp<S> &g, const uint32_t *Xs, const uint3
     return Z[0];
 }
 
-// Classical reduction: T + q*N over all 2*NP words (B_fma), result in T.
-// Returns the carry out of the top word (C = T[NP..2NP) + carry * R).
+// Slot sums of the classical reduction T + q*N over all 2*NP words (B_fma): thread t's
+// slots t and G+t, T's words of each slot added before it is stored over them.
 template <class S>
-MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
+MPG_DI void fma_slots(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
     constexpr int G = S::G, M = S::M, A = S::A1;
-    uint32_t V[A];
-    zero<A>(V);
+    Acc3<M> acc;
+    acc3_zero<M>(acc);
     const AddendXform<M> addT{T};
     MPG_BLOCK_LOOP
     for (int j = 0; j < G; ++j) {
         const int v = (g.t - j) & (G - 1);
-        mac_block<M>(V, Qs + j * M, Ns + v * M);
+        mac_block<M>(acc, Qs + j * M, Ns + v * M);
         if (j == g.t) {   // add T's words of this slot, then store over them
+            uint32_t V[A];
+            acc3_value<M>(V, acc);
             addT(g.t, V);
-            flush<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
+            store_slot<M>(V, T + g.t * M, spill_of<S, M>(g, g.t));
+            acc3_zero<M>(acc);
         }
     }
-    addT(G + g.t, V);
-    flush<M>(V, T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
+    {
+        uint32_t V[A];
+        acc3_value<M>(V, acc);
+        addT(G + g.t, V);
+        store_slot<M>(V, T + (G + g.t) * M, spill_of<S, M>(g, G + g.t));
+    }
+}
+
+// Classical reduction: T + q*N, result in T. Returns the carry out of the top word
+// (C = T[NP..2NP) + carry * R).
+template <class S>
+MPG_DI uint32_t phase_fma(const Grp<S> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
+    constexpr int M = S::M;
+    fma_slots<S>(g, Qs, Ns, T);
     g.sync();
     uint32_t in0[M + 2];
     zero<M + 2>(in0);
@@ -856,11 +924,10 @@ MPG_DI void step_sqr(Grp<S> g) { phase_sqr<S>(g, g.X(), g.X(), g.T()); }   // sq
 // T (2*NP words) -> X = T * R^-1 mod N (q goes to Y). RED: 0 truncated (Alg. 6), 1 classical (Alg. 5).
 // lazy: no final subtraction; with 4N <= R and T < 4N^2 the result stays below 2N (the slack
 // that lets the paper's Alg. 3 and Alg. 5 skip it).
-template <class S, int RED>
-MPG_DI void step_reduce(Grp<S> g, bool lazy) {
+// c_add = [T mod R != 0] and low_zero = [T mod W^(NP-1) == 0], for the whole group
+template <class S>
+MPG_DI void reduce_flags(const Grp<S> &g, const uint32_t *T, uint32_t &c_add, uint32_t &low_zero) {
     constexpr int M = S::M, NP = S::NP;
-    uint32_t *T = g.T();
-    // c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0]
     uint32_t nz_all = 0u, nz_low = 0u;
     {
         uint32_t x[M];
@@ -874,8 +941,16 @@ MPG_DI void step_reduce(Grp<S> g, bool lazy) {
     const bool pr[2] = {nz_all != 0u, nz_low != 0u};
     uint32_t mk[2];
     g.template bits<2>(pr, mk);
-    const uint32_t c_add = mk[0] ? 1u : 0u;
-    const uint32_t low_zero = mk[1] ? 0u : 1u;
+    c_add = mk[0] ? 1u : 0u;
+    low_zero = mk[1] ? 0u : 1u;
+}
+
+template <class S, int RED>
+MPG_DI void step_reduce(Grp<S> g, bool lazy) {
+    constexpr int M = S::M, NP = S::NP;
+    uint32_t *T = g.T();
+    uint32_t c_add, low_zero;
+    reduce_flags<S>(g, T, c_add, low_zero);
     phase_mullo<S>(g, T, g.NI(), g.Q());
     if constexpr (RED == 0) {
         const uint32_t carry = phase_mulhi<S>(g, g.Q(), g.N(), T, c_add, low_zero, g.X());

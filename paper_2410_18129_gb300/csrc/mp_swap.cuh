@@ -1,0 +1,449 @@
+// Role-swapped groups for the Montgomery kernels of the block-product reductions
+// (truncated, Alg. 6; classical, Alg. 3/5).
+//
+// A block holds 32 instances in G warps and every instance keeps one record of shared
+// memory, as in mp_group.cuh. The same records are worked on under two thread mappings:
+//   * product view: warp t plays thread t of all 32 instances (lane = instance). The block
+//     products of a phase then run with a warp-uniform thread index: each slot gets its own
+//     loop of exactly its block count, and a slot is stored when its loop ends (no
+//     thread-dependent slot switch inside a loop). Global loads and stores of an instance's
+//     words (operands, context, window-table scans) are coalesced across the 32 instances.
+//   * carry view: the G threads of an instance are G consecutive lanes of one warp (32/G
+//     instances per warp). Carry resolution, the c_add / low-zero tests, the group sum of
+//     the Thm. 2 boundary terms and the final subtraction use shuffles and ballots there.
+// A block barrier separates the two views; a Montgomery product crosses six of them.
+#pragma once
+#include "mp_kernels.cuh"
+
+namespace mpg {
+
+template <int G_, int M_>
+struct Swap {
+    using PS = Shape<G_, M_, true>;    // product view
+    using LS = Shape<G_, M_, false>;   // carry view
+    static constexpr int G = G_, M = M_, NP = G_ * M_, H = M_ / 2;
+    static constexpr int TPB = 32 * G_;   // 32 instances per block
+    static_assert(PS::OFF_P == LS::OFF_P && PS::OFF_T == LS::OFF_T, "one record layout for both views");
+    static_assert(LS::MONT_OK, "Montgomery needs an even M >= 4");
+    // record: operands, T, spills (the views' exchange words are not used)
+    static constexpr int WORDS_RAW = LS::OFF_P + 2 * G_ * (M_ + 1);
+    // product view: the 32 lanes of a warp read the same offset of 32 records; a stride of
+    // 4 (mod 8) words puts each group of 8 lanes' 16-byte accesses on distinct banks
+    static constexpr int WORDS = ((WORDS_RAW + 3) / 8) * 8 + 4;
+    static constexpr size_t SMEM = (size_t)32 * WORDS * 4;
+};
+
+template <class W>
+struct Views {
+    Grp<typename W::PS> p;   // product view
+    Grp<typename W::LS> l;   // carry view
+};
+
+template <class W>
+MPG_DI Views<W> swap_views(uint32_t *smem) {
+    Views<W> v;
+    const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5);
+    v.p.sm = smem + lane * W::WORDS;
+    v.p.pa = v.p.sm + W::LS::OFF_P;
+    v.p.t = warp;
+    v.p.gbase = 0;
+    const int li = warp * (32 / W::G) + lane / W::G;
+    v.l.sm = smem + li * W::WORDS;
+    v.l.pa = v.l.sm + W::LS::OFF_P;
+    v.l.t = lane % W::G;
+    v.l.gbase = lane & ~(W::G - 1);
+    return v;
+}
+
+// instance of the product view in the launch
+MPG_DI size_t swap_instance() { return (size_t)blockIdx.x * 32 + (threadIdx.x & 31); }
+
+MPG_DI void bsync() { __syncthreads(); }
+
+// ------------------------------------------------------------------ product-view phases
+
+// V (2M+2 words, below W^(2M+1) / 2) <- 2 V + the squares x_i^2 at columns 2i
+template <int M>
+MPG_DI void double_add_diag(uint32_t (&V)[2 * M + 2], const uint32_t (&x)[M]) {
+#pragma unroll
+    for (int k = 2 * M + 1; k > 0; --k) V[k] = __funnelshift_l(V[k - 1], V[k], 1);
+    V[0] <<= 1;
+    mad_lo_cc(V[0], x[0], x[0]);
+    madc_hi_cc(V[1], x[0], x[0]);
+#pragma unroll
+    for (int i = 1; i < M; ++i) {
+        madc_lo_cc(V[2 * i], x[i], x[i]);
+        madc_hi_cc(V[2 * i + 1], x[i], x[i]);
+    }
+    addc_cc(V[2 * M], 0u);
+    addc(V[2 * M + 1], 0u);
+}
+
+// Slot sums of T = X^2 in the product view, complete (no transform left for the resolve).
+// Thread t owns slots t and G+t (the cross products X_u X_v, u < v, on those diagonals). The
+// square of block u covers exactly the columns of slot 2u, so the owner of an even slot s
+// (an even t: both of its slots are even) adds X_{s/2}^2 itself: the block's cross terms
+// join the accumulator before the doubling, its squares x_i^2 after it. Every slot sum stays
+// below (G + 2) W^(2M) < W^(2M+1).
+template <class W>
+MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint32_t *T) {
+    using S = typename W::PS;
+    constexpr int G = W::G, M = W::M;
+    const int t = g.t;
+    const bool even = (t & 1) == 0;
+    const int nA = (t + 1) >> 1;              // pairs u < v with u + v = t
+    const int nB = ((G - t + 1) >> 1) - 1;    // pairs with u + v = G + t
+    Acc3<M> a;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = k ? G + t : t;
+        acc3_zero<M>(a);
+        if (k == 0) {
+            MPG_BLOCK_LOOP
+            for (int u = 0; u < nA; ++u) mac_block<M>(a, X + u * M, X + (t - u) * M);
+        } else {
+            MPG_BLOCK_LOOP
+            for (int j = 0; j < nB; ++j) {
+                const int u = t + 1 + j;
+                mac_block<M>(a, X + u * M, X + (G + t - u) * M);
+            }
+        }
+        uint32_t x[M];
+        if (even) {   // warp-uniform
+            lds<M>(x, X + (s >> 1) * M);
+            acc3_tri<M>(a, x);
+        } else {
+            zero<M>(x);
+        }
+        uint32_t V[2 * M + 2];
+        acc3_value<M>(V, a);
+        double_add_diag<M>(V, x);
+        store_slot<M>(V, T + s * M, spill_of<S, M>(g, s));
+    }
+}
+
+// Slot sums of the truncated high half C = floor(T/R) + floor(qN/R) (Alg. 6) in the product
+// view: the block products of qN with u + v >= 2G in H-word slots (thread t: slots t and
+// 2G-1-t), T's high words of each slot added before it is stored, and this thread's share
+// of the Thm. 2 boundary sum parked in T's low half (dead once q is formed; word NP-1 kept).
+template <class W>
+MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *C,
+                            const uint32_t *Thi) {
+    using S = typename W::PS;
+    constexpr int G = W::G, H = W::H, NP = W::NP;
+    const int t = g.t;
+    {
+        uint32_t Z[H + 3];
+        zero<H + 3>(Z);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {   // upper triangles of the diagonal blocks u + v = 2G-1
+            const int u = 2 * t + j;
+            tri_mac<H>(Z, Qs + u * H, Ns + (2 * G - 1 - u) * H);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {   // corner hi halves of the blocks u + v = 2G-2
+            const int u = 2 * t + j;
+            const bool live = u <= 2 * G - 2;
+            const uint32_t xq = Qs[u * H + H - 1];
+            const uint32_t yn = live ? Ns[(2 * G - 2 - u) * H + H - 1] : 0u;
+            add_word<H + 3>(Z, __umulhi(xq, yn));
+        }
+        static_assert(G * (H + 3) <= NP - 1, "Z exchange must stay below word NP-1 of T");
+        uint32_t *zs = g.T() + t * (H + 3);
+#pragma unroll
+        for (int k = 0; k < H + 3; ++k) zs[k] = Z[k];
+    }
+    const AddendXform<H> addT{Thi};
+    Acc3<H> a;
+    acc3_zero<H>(a);
+    const auto none = [](int) {};
+    mac_loop_pipelined<H>(a, Qs, Ns, 2 * G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; },
+                          none);
+    {
+        uint32_t V[2 * H + 2];
+        acc3_value<H>(V, a);
+        addT(t, V);
+        store_slot<H>(V, C + t * H, spill_of<S, H>(g, t));
+    }
+    acc3_zero<H>(a);
+    if (t > 0)   // slot 2G-1-t of thread t has t products (none for thread 0)
+        mac_loop_pipelined<H>(a, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; }, none);
+    {
+        uint32_t V[2 * H + 2];
+        acc3_value<H>(V, a);
+        addT(2 * G - 1 - t, V);
+        store_slot<H>(V, C + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
+    }
+}
+
+// X <- X * Y * R^-1 mod N, or X^2 * R^-1 mod N (Y then unused); Y holds q afterwards.
+// On entry the operands are in shared memory behind a block barrier; on exit X holds the
+// result behind a block barrier. lazy: no final subtraction (results < 2N when 4N <= R).
+template <class W, int RED>
+MPG_DI void swap_mont(const Views<W> &v, bool square, bool lazy) {
+    using PS = typename W::PS;
+    using LS = typename W::LS;
+    constexpr int M = W::M, H = W::H, NP = W::NP, G = W::G;
+    const Grp<PS> &gp = v.p;
+    const Grp<LS> &gl = v.l;
+    // 1. T = X * Y or X^2 (slot sums in the product view, carries in the carry view)
+    if (square) swp_sqr_slots<W>(gp, gp.X(), gp.T());
+    else mul_slots<PS>(gp, gp.X(), gp.Y(), gp.T());
+    bsync();
+    {
+        uint32_t in0[M + 2];
+        zero<M + 2>(in0);
+        resolve<LS, M, PAT_SEQ>(gl, in0, NoXform{}, gl.T());
+    }
+    uint32_t c_add, low_zero;
+    reduce_flags<LS>(gl, gl.T(), c_add, low_zero);
+    bsync();
+    // 2. q = T_lo * N' mod R
+    mullo_slots<PS>(gp, gp.T(), gp.NI(), gp.Q());
+    bsync();
+    {
+        uint32_t in0[H + 2];
+        zero<H + 2>(in0);
+        resolve<LS, H, PAT_ZIGZAG>(gl, in0, NoXform{}, gl.Q());
+    }
+    bsync();
+    if constexpr (RED == 0) {
+        // 3. C = floor(T/R) + floor(qN/R) + c_add from the high half of qN (Thm. 2)
+        swp_mulhi_slots<W>(gp, gp.Q(), gp.N(), gp.X(), gp.T() + NP);
+        bsync();
+        uint32_t Z[H + 3];
+        lds<H + 3>(Z, gl.T() + gl.t * (H + 3));
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {   // sum over the instance's G lanes
+            uint32_t o[H + 3];
+#pragma unroll
+            for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
+            add_n<H + 3>(Z, o);
+        }
+        const uint32_t carry = mulhi_resolve<LS>(gl, Z, gl.T(), c_add, low_zero, gl.X(), NoXform{});
+        if (!lazy) cond_sub<LS>(gl, gl.X(), carry, gl.N(), gl.X());
+    } else {
+        // 3. classical: T + q*N over all words, C = its high half
+        (void)c_add;
+        (void)low_zero;
+        fma_slots<PS>(gp, gp.Q(), gp.N(), gp.T());
+        bsync();
+        uint32_t in0[M + 2];
+        zero<M + 2>(in0);
+        const uint32_t carry = resolve<LS, M, PAT_SEQ>(gl, in0, NoXform{}, gl.T());
+        if (!lazy) {
+            cond_sub<LS>(gl, gl.T() + NP, carry, gl.N(), gl.X());
+        } else {
+            uint32_t x[M];
+            lds<M>(x, gl.T() + NP + gl.t * M);
+            sts<M>(gl.X() + gl.t * M, x);
+        }
+    }
+    bsync();
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <class W>
+constexpr int swap_blocks_per_sm() {
+    constexpr long smem = (long)W::SMEM + 1024;
+    constexpr long b = 233472L / smem;
+    return b < 1 ? 1 : (int)b;
+}
+
+template <class W, int RED>
+__global__ void __launch_bounds__(W::TPB, (swap_blocks_per_sm<W>())) k_mont_swap(KArgs A) {
+    extern __shared__ uint4 smem4[];
+    const Views<W> v = swap_views<W>(reinterpret_cast<uint32_t *>(smem4));
+    using PS = typename W::PS;
+    const Grp<PS> &g = v.p;
+    const size_t k = swap_instance();
+    const bool valid = k < A.batch;
+    load_ctx<PS>(g, g.N(), A.N, A, k, valid);
+    load_ctx<PS>(g, g.NI(), A.NI, A, k, valid);
+    load_api<PS>(g, g.X(), A.a, A, k, valid);
+    if (!A.square) load_api<PS>(g, g.Y(), A.b, A, k, valid);
+    bsync();
+    for (int r = 0; r <= (A.correct ? 1 : 0); ++r) {
+        if (r) {
+            load_ctx<PS>(g, g.Y(), A.K, A, k, valid);
+            bsync();
+        }
+        swap_mont<W, RED>(v, r == 0 && A.square != 0, false);
+    }
+    uint32_t x[W::M];
+    lds<W::M>(x, g.X() + g.t * W::M);
+    gstore<W::M>(A.out, x, A.layout, k, valid, g.t * W::M, A.n, A.batch);
+}
+
+// Constant-time exponentiation (Alg. 7) in the role-swapped mapping: the same schedule as
+// modexp_group, with table accesses and global loads in the product view.
+template <class W, int RED>
+MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
+    using PS = typename W::PS;
+    constexpr int M = W::M;
+    const Grp<PS> &g = v.p;
+    bool valid = k < A.batch;
+    const size_t kc = (A.index && valid) ? (size_t)A.index[k] : k;   // routing: public
+    valid = valid && kc < A.cbatch;
+    const int w = A.window;
+    const int E = 1 << w;
+    const size_t cb = A.cbatch;
+    uint4 *tab = reinterpret_cast<uint4 *>(A.table);
+
+    auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
+        uint32_t x[M];
+        lds<M>(x, src + g.t * M);
+        if (!valid) return;
+        if constexpr (M % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < M / 4; ++c)
+                tab[tidx4<PS>(e, g.t * (M / 4) + c, kc, cb)] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const int i = g.t * M + j;
+                A.table[tidx4<PS>(e, i >> 2, kc, cb) * 4 + (i & 3)] = x[j];
+            }
+        }
+    };
+    auto fetch = [&](int e, uint32_t (&x)[M]) {     // table entry e -> this thread's M words
+        if constexpr (M % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < M / 4; ++c) {
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (valid) q = tab[tidx4<PS>(e, g.t * (M / 4) + c, kc, cb)];
+                x[4 * c] = q.x; x[4 * c + 1] = q.y; x[4 * c + 2] = q.z; x[4 * c + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const int i = g.t * M + j;
+                x[j] = valid ? A.table[tidx4<PS>(e, i >> 2, kc, cb) * 4 + (i & 3)] : 0u;
+            }
+        }
+    };
+
+    load_ctx<PS>(g, g.N(), A.N, A, kc, valid);
+    load_ctx<PS>(g, g.NI(), A.NI, A, kc, valid);
+    const int nbuild = A.mode != 2 ? E - 1 : 0;
+    const int windows = (A.ebits + w - 1) / w;
+    const int nwin = A.mode != 1 ? windows * (w + 1) + 1 : 0;
+    if (A.mode != 2) {
+        load_api<PS>(g, g.X(), A.a, A, kc, valid);
+        load_ctx<PS>(g, g.Y(), A.R2, A, kc, valid);
+    } else {
+        load_ctx<PS>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form
+    }
+    bsync();
+    for (int op = 0; op < nbuild + nwin; ++op) {
+        bool square = false;
+        if (op >= nbuild) {
+            const int r = op - nbuild;
+            const int i = r / (w + 1), s = r - i * (w + 1);
+            if (i == windows) {                         // the product with 1
+                uint32_t x[M];
+                zero<M>(x);
+                if (g.t == 0) x[0] = 1u;
+                sts<M>(g.Y() + g.t * M, x);
+                bsync();
+            } else if (s < w) {
+                square = true;
+            } else {   // masked scan of the whole table: every entry is read, one is kept
+                const uint32_t bsel = window_bits(A, k, valid, (windows - 1 - i) * w, w);
+                uint32_t acc[M];
+                zero<M>(acc);
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t m = mask_if_equal((uint32_t)e, bsel);
+                    uint32_t x[M];
+                    fetch(e, x);
+#pragma unroll
+                    for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
+                }
+                sts<M>(g.Y() + g.t * M, acc);
+                bsync();
+            }
+        }
+        swap_mont<W, RED>(v, square, A.lazy != 0);
+        if (op < nbuild) {
+            put(op + 1, g.X());
+            if (op == 0) {                              // G[0] = R mod N
+                load_ctx<PS>(g, g.Y(), A.R1, A, kc, valid);
+                put(0, g.Y());
+            }
+            if (op + 1 < nbuild) {                      // next: G[op+2] = G[op+1] * G[1]
+                uint32_t x[M];                          // (the product leaves q in Y)
+                fetch(1, x);
+                sts<M>(g.Y() + g.t * M, x);
+            } else if (A.mode == 0) {
+                load_ctx<PS>(g, g.X(), A.R1, A, kc, valid);   // Y_acc = 1 in Montgomery form
+            }
+            bsync();
+        }
+    }
+    if (A.mode == 1) return;
+    if (A.lazy) {   // X <= N here: one subtraction makes it canonical (carry view)
+        cond_sub<typename W::LS>(v.l, v.l.X(), 0u, v.l.N(), v.l.X());
+        bsync();
+    }
+    uint32_t x[M];
+    lds<M>(x, g.X() + g.t * M);
+    gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
+}
+
+template <class W, int RED>
+__global__ void __launch_bounds__(W::TPB, (swap_blocks_per_sm<W>())) k_modexp_swap(KArgs A) {
+    extern __shared__ uint4 smem4[];
+    const Views<W> v = swap_views<W>(reinterpret_cast<uint32_t *>(smem4));
+    modexp_swap<W, RED>(v, A, swap_instance());
+}
+
+// launchers: red 0 truncated, 1 classical; the word-serial reduction (red 2) passes a word
+// between the threads of an instance at every step and keeps the lane-mapped kernels
+template <class W, int KIND, class F>
+static cudaError_t launch_swap(F kern, const KArgs &A, cudaStream_t st) {
+    static std::atomic<unsigned long long> attr_done{0ull};
+    const cudaError_t e = smem_attr_once(attr_done, kern, W::SMEM);
+    if (e != cudaSuccess) return e;
+    const size_t blocks = (A.batch + 31) / 32;
+    kern<<<(unsigned)blocks, W::TPB, W::SMEM, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <class W, class Lane>
+struct SwapImpl {
+    static cudaError_t mont(const KArgs &A, cudaStream_t st) {
+        if (A.red == 2) return Lane::mont(A, st);
+        return A.red ? launch_swap<W, 1>(k_mont_swap<W, 1>, A, st) : launch_swap<W, 0>(k_mont_swap<W, 0>, A, st);
+    }
+    static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
+        if (A.red == 2) return Lane::modexp(A, st);
+        return A.red ? launch_swap<W, 3>(k_modexp_swap<W, 1>, A, st) : launch_swap<W, 2>(k_modexp_swap<W, 0>, A, st);
+    }
+};
+
+}  // namespace mpg
+
+// a lane-mapped shape whose truncated and classical Montgomery kernels run role-swapped
+#define MPG_DEFINE_SHAPE_SWAP(G, M, TPB)                                                     \
+    namespace mpg {                                                                          \
+    ShapeOps shape_ops_##G##_##M() {                                                         \
+        using Lane = ShapeImpl<Shape<G, M>, TPB>;                                            \
+        ShapeOps o = Lane::ops();                                                            \
+        o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
+        o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
+        return o;                                                                            \
+    }                                                                                        \
+    }
+
+#define MPG_DEFINE_SHAPE_KARA_SWAP(G, M, TPB, MH, TPBK)                                      \
+    namespace mpg {                                                                          \
+    ShapeOps shape_ops_##G##_##M() {                                                         \
+        using Lane = ShapeImpl<Shape<G, M>, TPB>;                                            \
+        ShapeOps o = Lane::ops();                                                            \
+        o.kara = &launch_kara<Shape<G, M>, Shape<G, MH>, TPBK>;                              \
+        o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
+        o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
+        return o;                                                                            \
+    }                                                                                        \
+    }

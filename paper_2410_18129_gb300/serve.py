@@ -142,13 +142,17 @@ def serve(trace, executor, slots: int = 4, max_batch: int = 8192, admission: Adm
 # ------------------------------------------------------------------ GPU side
 
 class Pool:
-    """Resident moduli with fixed bases: per size a context and its window tables."""
+    """Resident moduli with fixed bases: per size a context and its window tables.
 
-    def __init__(self, mp, seed: int = 0, count: int = 4096, windows: dict | None = None):
+    sizes[k] is the bit size of pool entry k; moduli[bits] and bases[bits] hold, in entry
+    order, the moduli and fixed bases of the entries of that size (uint32 words, one row
+    per entry, bases below their moduli)."""
+
+    def __init__(self, mp, sizes, moduli: dict, bases: dict, windows: dict | None = None):
         import torch
-        import seeded_inputs as si
         self.mp, self.torch = mp, torch
-        self.sizes = si.pool_sizes(seed, count)
+        self.sizes = np.asarray(sizes)
+        count = self.sizes.size
         self.local = np.zeros(count, dtype=np.int64)
         self.classes = {}
         windows = windows or {}
@@ -156,12 +160,14 @@ class Pool:
         for bits in sorted(set(int(b) for b in self.sizes)):
             ids = np.nonzero(self.sizes == bits)[0]
             self.local[ids] = np.arange(ids.size)
-            b = si.make_batch(seed, "serving", ids.size, bits, ebits=1, sub=bits)
-            ctx = mp.MontCtx(dev(b.N), ids.size, bits, IL)
+            N, g = np.asarray(moduli[bits], dtype=np.uint32), np.asarray(bases[bits], dtype=np.uint32)
+            if N.shape[0] != ids.size or g.shape != N.shape:
+                raise ValueError(f"{bits}-bit entries: {ids.size} in sizes, moduli {N.shape}, bases {g.shape}")
+            ctx = mp.MontCtx(dev(N), ids.size, bits, IL)
             w = int(windows.get(bits) or mp.tune_get(bits)["window"])
             tables = torch.empty(mp.modexp_table_bytes(ctx, w) // 4, dtype=torch.int32, device="cuda")
-            mp.modexp_table_build(tables, dev(b.a), ctx, w)
-            self.classes[bits] = {"ctx": ctx, "tables": tables, "window": w, "N": b.N, "g": b.a, "n": b.n,
+            mp.modexp_table_build(tables, dev(g), ctx, w)
+            self.classes[bits] = {"ctx": ctx, "tables": tables, "window": w, "N": N, "g": g, "n": N.shape[1],
                                   "ids": ids}
         torch.cuda.synchronize()
 
@@ -277,16 +283,3 @@ class PlainExecutor(_GpuExecutorBase):
 
     def done(self, h) -> bool:
         return True
-
-
-def expected(pool: Pool, trace, reqs, oracle):
-    """Oracle results of the given requests (test infrastructure)."""
-    out = {}
-    for r in reqs:
-        k = int(trace.entry[r])
-        bits = int(pool.sizes[k])
-        c = pool.classes[bits]
-        j = int(pool.local[k])
-        y = oracle.modexp(c["g"][j:j + 1], trace.exponents[r][None, :], bits, c["N"][j:j + 1])
-        out[int(r)] = y[0]
-    return out

@@ -292,6 +292,27 @@ def pool_sizes(seed: int, count: int) -> np.ndarray:
     return mixed_sizes(seed + 1000, count)
 
 
+@dataclass
+class PoolInputs:
+    """A resident serving pool: entry k has sizes[k] bits; moduli[bits] and bases[bits] list the
+    moduli and fixed bases of the entries of that size in entry order."""
+    sizes: np.ndarray
+    moduli: dict
+    bases: dict
+
+
+def serving_pool(seed: int, count: int) -> PoolInputs:
+    """``count`` pool entries with the mixed-size distribution: random odd moduli and one
+    uniform fixed base below each."""
+    sizes = pool_sizes(seed, count)
+    moduli, bases = {}, {}
+    for bits in sorted(set(int(b) for b in sizes)):
+        cnt = int((sizes == bits).sum())
+        b = make_batch(seed, "serving", cnt, bits, ebits=1, sub=bits)
+        moduli[bits], bases[bits] = b.N, b.a
+    return PoolInputs(sizes, moduli, bases)
+
+
 def poisson_trace(seed: int, rate: float, count: int, sizes: np.ndarray) -> Trace:
     """``count`` requests with exponential inter-arrival gaps of mean 1/rate, each picking a
     pool entry uniformly and carrying a fresh full-length exponent for that entry's size."""
