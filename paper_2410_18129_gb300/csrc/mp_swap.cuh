@@ -61,6 +61,60 @@ MPG_DI size_t swap_instance() { return (size_t)blockIdx.x * 32 + (threadIdx.x & 
 MPG_DI void bsync() { __syncthreads(); }
 
 // ------------------------------------------------------------------ product-view phases
+//
+// Thread t of every instance is warp t here, so each slot's blocks form one run of mac_run
+// with a warp-uniform count, and a slot is stored straight after its run.
+
+// slot sums of T = X * Y: thread t owns slots t (X_j Y_{t-j}, j <= t) and G+t (j > t)
+template <class W>
+MPG_DI void swp_mul_slots(const Grp<typename W::PS> &g, const uint32_t *X, const uint32_t *Y, uint32_t *T) {
+    using S = typename W::PS;
+    constexpr int G = W::G, M = W::M, U = run_group<M>();
+    const int t = g.t;
+    Acc3<M> a;
+    acc3_zero<M>(a);
+    mac_run<M, U>(a, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
+    flush<M>(a, T + t * M, spill_of<S, M>(g, t));
+    mac_run<M, U>(a, X, Y, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
+    park<M>(a, T + (G + t) * M, spill_of<S, M>(g, G + t));
+}
+
+// slot sums of q = T_lo * N' mod R in H-word slots: thread t owns slots t (t+1 blocks) and
+// 2G-1-t (2G-t blocks)
+template <class W>
+MPG_DI void swp_mullo_slots(const Grp<typename W::PS> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
+    using S = typename W::PS;
+    constexpr int G = W::G, H = W::H, U = run_group<H>();
+    const int t = g.t;
+    Acc3<H> a;
+    acc3_zero<H>(a);
+    mac_run<H, U>(a, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
+    flush<H>(a, Q + t * H, spill_of<S, H>(g, t));
+    mac_run<H, U>(a, X, Y, 2 * G - t, [&](int j, int &u, int &v) { u = j; v = 2 * G - 1 - t - j; });
+    park<H>(a, Q + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
+}
+
+// slot sums of the classical reduction T + q*N over all 2*NP words: T's words of a slot are
+// added before the slot is stored over them
+template <class W>
+MPG_DI void swp_fma_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
+    using S = typename W::PS;
+    constexpr int G = W::G, M = W::M, U = run_group<M>();
+    const int t = g.t;
+    const AddendXform<M> addT{T};
+    Acc3<M> a;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = k ? G + t : t;
+        acc3_zero<M>(a);
+        if (k == 0) mac_run<M, U>(a, Qs, Ns, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
+        else mac_run<M, U>(a, Qs, Ns, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
+        uint32_t V[2 * M + 2];
+        acc3_value<M>(V, a);
+        addT(s, V);
+        store_slot<M>(V, T + s * M, spill_of<S, M>(g, s));
+    }
+}
 
 // V (2M+2 words, below W^(2M+1) / 2) <- 2 V + the squares x_i^2 at columns 2i
 template <int M>
@@ -98,16 +152,8 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
     for (int k = 0; k < 2; ++k) {
         const int s = k ? G + t : t;
         acc3_zero<M>(a);
-        if (k == 0) {
-            MPG_BLOCK_LOOP
-            for (int u = 0; u < nA; ++u) mac_block<M>(a, X + u * M, X + (t - u) * M);
-        } else {
-            MPG_BLOCK_LOOP
-            for (int j = 0; j < nB; ++j) {
-                const int u = t + 1 + j;
-                mac_block<M>(a, X + u * M, X + (G + t - u) * M);
-            }
-        }
+        if (k == 0) mac_run<M, run_group<M>()>(a, X, X, nA, [&](int j, int &u, int &v) { u = j; v = t - j; });
+        else mac_run<M, run_group<M>()>(a, X, X, nB, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
         uint32_t x[M];
         if (even) {   // warp-uniform
             lds<M>(x, X + (s >> 1) * M);
@@ -122,6 +168,60 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
     }
 }
 
+// Boundary terms of Thm. 2 for one H x H block product X*Y on the diagonal u + v = 2G-1, whose
+// local column c = i+j sits at global column NP-H+c; Z word 0 is column NP-1. Needed: the
+// pairs with c >= H-1 in full (Z words c-H+1, c-H+2) and the hi halves of the pairs with
+// c = H-2 (Z word 0). In row i the pairs c >= H-1 are j = H-1-i .. H-1: a chain over every
+// other j starts at Z word 0 (pairs at even words, ZE) and one at Z word 1 (odd words, ZO,
+// ZO[k] = word k+1); their carries go to counters ZK. The hi halves go to the two-word zh.
+template <int H>
+struct ZAcc {
+    static constexpr int LE = (H + 2) & ~1;   // even pairs up to word H
+    uint32_t E[LE];
+    uint32_t O[LE];
+    uint32_t K[H + 3];
+    uint32_t h0, h1;
+};
+
+template <int H, int I>
+MPG_DI void zacc_row(ZAcc<H> &z, uint32_t xi, const uint32_t (&y)[H]) {
+    constexpr int J0A = H - 1 - I, NA = I / 2 + 1;   // chain A: j = H-1-I, H+1-I, ...
+    acc3_chain<H, ZAcc<H>::LE, J0A, 0, NA>(z.E, z.K[2 * NA], xi, y);
+    if constexpr (I >= 1) {
+        constexpr int J0B = H - I, NB = (I - 1) / 2 + 1;   // chain B: j = H-I, H-I+2, ...
+        acc3_chain<H, ZAcc<H>::LE, J0B, 0, NB>(z.O, z.K[2 * NB + 1], xi, y);
+    }
+    if constexpr (I <= H - 2) {   // hi half of x_I * y_{H-2-I} (column H-2)
+        mad_hi_cc(z.h0, xi, y[H - 2 - I]);
+        addc(z.h1, 0u);
+    }
+}
+
+template <int H, int I = 0>
+MPG_DI void zacc_rows(ZAcc<H> &z, const uint32_t (&x)[H], const uint32_t (&y)[H]) {
+    if constexpr (I < H) {
+        zacc_row<H, I>(z, x[I], y);
+        zacc_rows<H, I + 1>(z, x, y);
+    }
+}
+
+// Z[0 .. H+3) = value of z
+template <int H>
+MPG_DI void zacc_value(uint32_t (&Z)[H + 3], const ZAcc<H> &z) {
+    constexpr int LE = ZAcc<H>::LE;
+#pragma unroll
+    for (int k = 0; k < H + 3; ++k) Z[k] = k < LE ? z.E[k] : 0u;
+    add_cc(Z[1], z.O[0]);
+#pragma unroll
+    for (int k = 1; k < LE && k + 1 < H + 3; ++k) addc_cc(Z[k + 1], z.O[k]);
+#pragma unroll
+    for (int k = LE + 1; k < H + 3; ++k) addc_cc(Z[k], 0u);
+    add_cc(Z[0], z.h0);
+    addc_cc(Z[1], z.h1);
+#pragma unroll
+    for (int k = 2; k < H + 3; ++k) addc_cc(Z[k], z.K[k]);
+}
+
 // Slot sums of the truncated high half C = floor(T/R) + floor(qN/R) (Alg. 6) in the product
 // view: the block products of qN with u + v >= 2G in H-word slots (thread t: slots t and
 // 2G-1-t), T's high words of each slot added before it is stored, and this thread's share
@@ -133,12 +233,19 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
     constexpr int G = W::G, H = W::H, NP = W::NP;
     const int t = g.t;
     {
-        uint32_t Z[H + 3];
-        zero<H + 3>(Z);
+        ZAcc<H> z;
+        zero<ZAcc<H>::LE>(z.E);
+        zero<ZAcc<H>::LE>(z.O);
+        zero<H + 3>(z.K);
+        z.h0 = 0u;
+        z.h1 = 0u;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {   // upper triangles of the diagonal blocks u + v = 2G-1
+        for (int j = 0; j < 2; ++j) {   // boundary terms of the diagonal blocks u + v = 2G-1
             const int u = 2 * t + j;
-            tri_mac<H>(Z, Qs + u * H, Ns + (2 * G - 1 - u) * H);
+            uint32_t x[H], y[H];
+            lds<H>(x, Qs + u * H);
+            lds<H>(y, Ns + (2 * G - 1 - u) * H);
+            zacc_rows<H>(z, x, y);
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {   // corner hi halves of the blocks u + v = 2G-2
@@ -146,8 +253,11 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
             const bool live = u <= 2 * G - 2;
             const uint32_t xq = Qs[u * H + H - 1];
             const uint32_t yn = live ? Ns[(2 * G - 2 - u) * H + H - 1] : 0u;
-            add_word<H + 3>(Z, __umulhi(xq, yn));
+            mad_hi_cc(z.h0, xq, yn);
+            addc(z.h1, 0u);
         }
+        uint32_t Z[H + 3];
+        zacc_value<H>(Z, z);
         static_assert(G * (H + 3) <= NP - 1, "Z exchange must stay below word NP-1 of T");
         uint32_t *zs = g.T() + t * (H + 3);
 #pragma unroll
@@ -156,9 +266,8 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
     const AddendXform<H> addT{Thi};
     Acc3<H> a;
     acc3_zero<H>(a);
-    const auto none = [](int) {};
-    mac_loop_pipelined<H>(a, Qs, Ns, 2 * G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; },
-                          none);
+    constexpr int U = run_group<H>();
+    mac_run<H, U>(a, Qs, Ns, 2 * G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; });
     {
         uint32_t V[2 * H + 2];
         acc3_value<H>(V, a);
@@ -166,8 +275,7 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
         store_slot<H>(V, C + t * H, spill_of<S, H>(g, t));
     }
     acc3_zero<H>(a);
-    if (t > 0)   // slot 2G-1-t of thread t has t products (none for thread 0)
-        mac_loop_pipelined<H>(a, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; }, none);
+    mac_run<H, U>(a, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; });
     {
         uint32_t V[2 * H + 2];
         acc3_value<H>(V, a);
@@ -188,7 +296,7 @@ MPG_DI void swap_mont(const Views<W> &v, bool square, bool lazy) {
     const Grp<LS> &gl = v.l;
     // 1. T = X * Y or X^2 (slot sums in the product view, carries in the carry view)
     if (square) swp_sqr_slots<W>(gp, gp.X(), gp.T());
-    else mul_slots<PS>(gp, gp.X(), gp.Y(), gp.T());
+    else swp_mul_slots<W>(gp, gp.X(), gp.Y(), gp.T());
     bsync();
     {
         uint32_t in0[M + 2];
@@ -199,7 +307,7 @@ MPG_DI void swap_mont(const Views<W> &v, bool square, bool lazy) {
     reduce_flags<LS>(gl, gl.T(), c_add, low_zero);
     bsync();
     // 2. q = T_lo * N' mod R
-    mullo_slots<PS>(gp, gp.T(), gp.NI(), gp.Q());
+    swp_mullo_slots<W>(gp, gp.T(), gp.NI(), gp.Q());
     bsync();
     {
         uint32_t in0[H + 2];
@@ -226,7 +334,7 @@ MPG_DI void swap_mont(const Views<W> &v, bool square, bool lazy) {
         // 3. classical: T + q*N over all words, C = its high half
         (void)c_add;
         (void)low_zero;
-        fma_slots<PS>(gp, gp.Q(), gp.N(), gp.T());
+        swp_fma_slots<W>(gp, gp.Q(), gp.N(), gp.T());
         bsync();
         uint32_t in0[M + 2];
         zero<M + 2>(in0);
