@@ -461,12 +461,22 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
                 const uint32_t bsel = window_bits(A, k, valid, (windows - 1 - i) * w, w);
                 uint32_t acc[M];
                 zero<M>(acc);
-                for (int e = 0; e < E; ++e) {
-                    const uint32_t m = mask_if_equal((uint32_t)e, bsel);
-                    uint32_t x[M];
-                    fetch(e, x);
+                // two entries per iteration: their loads are in flight together (measured best
+                // of 1, 2, 4, 8: 2048-bit modexp 306.3k, 310.5k, 307.9k, 308.4k/s)
+                constexpr int SCAN = 2;
+                for (int e0 = 0; e0 < E; e0 += SCAN) {
+                    uint32_t x[SCAN][M];
 #pragma unroll
-                    for (int j = 0; j < M; ++j) acc[j] |= x[j] & m;
+                    for (int r = 0; r < SCAN; ++r) {
+                        if (e0 + r < E) fetch(e0 + r, x[r]);
+                        else zero<M>(x[r]);
+                    }
+#pragma unroll
+                    for (int r = 0; r < SCAN; ++r) {
+                        const uint32_t m = mask_if_equal((uint32_t)(e0 + r), bsel);
+#pragma unroll
+                        for (int j = 0; j < M; ++j) acc[j] |= x[r][j] & m;
+                    }
                 }
                 sts<M>(g.Y() + g.t * M, acc);
                 bsync();
