@@ -209,17 +209,55 @@ __global__ void __launch_bounds__(768, 1) k_bench_acc(int iters, uint32_t seed, 
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// modes 13-14: 4x4 blocks with 256 threads per SM (latency exposed): 13 one split accumulator,
+// 14 two split accumulators taking alternate blocks (independent carry chains)
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) k_bench_ilp(int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
+    constexpr int B = 4;
+    uint32_t x[B], y[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) { x[i] = seed * (threadIdx.x + 3 * i + 1); y[i] = seed ^ (i * 0x9e3779b9u + threadIdx.x); }
+    uint32_t fold = 0u;
+    __syncthreads();
+    long long t0 = clock64();
+    Acc3<B> a, b;
+    acc3_zero<B>(a);
+    acc3_zero<B>(b);
+    for (int it = 0; it < iters; ++it) {
+        if constexpr (MODE == 13) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc3_mac<B>(a, x, y);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) { acc3_mac<B>(a, x, y); acc3_mac<B>(b, y, x); }
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) x[i] ^= a.E[i] + b.E[i];
+    }
+    uint32_t V[2 * B + 2], U[2 * B + 2];
+    acc3_value<B>(V, a);
+    acc3_value<B>(U, b);
+#pragma unroll
+    for (int j = 0; j < 2 * B + 2; ++j) fold ^= V[j] + U[j];
+    __syncthreads();
+    long long t1 = clock64();
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = fold;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 static void launch_acc(int mode, int sms, int iters, cudaStream_t st, uint32_t *sink, long long *cyc) {
     switch (mode) {
         case 9: k_bench_acc<9><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
         case 10: k_bench_acc<10><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
         case 11: k_bench_acc<11><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
+        case 13: k_bench_ilp<13><<<sms, 256, 0, st>>>(iters, 12345u, sink, cyc); break;
+        case 14: k_bench_ilp<14><<<sms, 256, 0, st>>>(iters, 12345u, sink, cyc); break;
         default: k_bench_acc<12><<<sms, 768, 0, st>>>(iters, 12345u, sink, cyc); break;
     }
 }
 
 extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream) {
-    if (mode < 0 || mode > 12 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
+    if (mode < 0 || mode > 14 || iters <= 0 || !per_clk_per_sm) return MP_ERR_ARG;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MP_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MP_ERR_CUDA;
@@ -255,7 +293,7 @@ extern "C" int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double
         // multiply-adds per thread: every mode is sized to 128 per iteration (mode 6: 256),
         // mode 7 runs on a quarter of the threads
         const double per_thread = (mode == 6 ? 256.0 : mode == 8 ? 200.0 : 128.0) * iters;
-        const double active = mode == 7 ? 256.0 : mode == 8 ? 512.0 : mode >= 9 ? 768.0 : (double)threads;
+        const double active = (mode == 7 || mode >= 13) ? 256.0 : mode == 8 ? 512.0 : mode >= 9 ? 768.0 : (double)threads;
         *per_clk_per_sm = per_thread * active / med;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);

@@ -241,8 +241,13 @@ MPG_DI void mac_loop_pipelined(Acc3<B> &V, const uint32_t *X, const uint32_t *Y,
 // per loop iteration the compiler splits the multiply-add pairs of the chains into separate
 // lo and hi instructions (measured: 654 instead of 273 multiply-pipe instructions for 272
 // partial products); with two full or four half blocks per iteration they stay paired.
-template <int B, int U, class UV>
-MPG_DI void mac_run(Acc3<B> &a, const uint32_t *X, const uint32_t *Y, int cnt, const UV &uv) {
+// xm maps the word offset u*B of X's block u to its place in X (identity by default).
+struct IdMap {
+    MPG_DI int operator()(int i) const { return i; }
+};
+
+template <int B, int U, class UV, class XM = IdMap>
+MPG_DI void mac_run(Acc3<B> &a, const uint32_t *X, const uint32_t *Y, int cnt, const UV &uv, const XM &xm = XM{}) {
     int j = 0;
     MPG_BLOCK_LOOP
     for (; j + U <= cnt; j += U) {
@@ -250,7 +255,7 @@ MPG_DI void mac_run(Acc3<B> &a, const uint32_t *X, const uint32_t *Y, int cnt, c
         for (int r = 0; r < U; ++r) {
             int u, v;
             uv(j + r, u, v);
-            mac_block<B>(a, X + u * B, Y + v * B);
+            mac_block<B>(a, X + xm(u * B), Y + v * B);
         }
     }
 #pragma unroll
@@ -258,7 +263,7 @@ MPG_DI void mac_run(Acc3<B> &a, const uint32_t *X, const uint32_t *Y, int cnt, c
         if (j + r < cnt) {
             int u, v;
             uv(j + r, u, v);
-            mac_block<B>(a, X + u * B, Y + v * B);
+            mac_block<B>(a, X + xm(u * B), Y + v * B);
         }
     }
 }

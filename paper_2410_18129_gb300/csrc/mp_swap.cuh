@@ -10,12 +10,26 @@
 //     words (operands, context, window-table scans) are coalesced across the 32 instances.
 //   * carry view: the G threads of an instance are G consecutive lanes of one warp (32/G
 //     instances per warp). Carry resolution, the c_add / low-zero tests, the group sum of
-//     the Thm. 2 boundary terms and the final subtraction use shuffles and ballots there.
+//     the Thm. 2 boundary terms and the final subtraction use shuffles and ballots there;
+//     each phase's resolve keeps its final words in registers, derives the flags or does the
+//     constant-time subtraction on them, and stores once.
 // A block barrier separates the two views; a Montgomery product crosses six of them.
+// T and the slot spill area are padded with four words after every 32: a carry-view thread
+// reads its M-word slots at stride M, and without the pad lanes t and t+4 of an instance
+// (M = 8) or lanes t, t+2, ... (M = 16) hit the same banks.
 #pragma once
 #include "mp_kernels.cuh"
 
 namespace mpg {
+
+// word offset of logical word i of a padded array (T, slot spills): four pad words follow
+// every 32 words. Blocks of 4 or 8 words never straddle a row, so they stay contiguous.
+MPG_DI int pad32(int i) { return i + ((i >> 5) << 2); }
+constexpr int pad_size(int n) { return n ? (n - 1) + (((n - 1) >> 5) << 2) + 1 : 0; }
+
+struct PadMap {
+    MPG_DI int operator()(int i) const { return pad32(i); }
+};
 
 template <int G_, int M_>
 struct Swap {
@@ -23,10 +37,15 @@ struct Swap {
     using LS = Shape<G_, M_, false>;   // carry view
     static constexpr int G = G_, M = M_, NP = G_ * M_, H = M_ / 2;
     static constexpr int TPB = 32 * G_;   // 32 instances per block
-    static_assert(PS::OFF_P == LS::OFF_P && PS::OFF_T == LS::OFF_T, "one record layout for both views");
     static_assert(LS::MONT_OK, "Montgomery needs an even M >= 4");
-    // record: operands, T, spills (the views' exchange words are not used)
-    static constexpr int WORDS_RAW = LS::OFF_P + 2 * G_ * (M_ + 1);
+    static_assert(M_ % 4 == 0 && 32 % M_ == 0 || M_ == 16, "padded rows hold whole blocks");
+    static_assert(PS::OFF_T == LS::OFF_T, "one record layout for both views");
+    // record: X, Y (q), N, N' (NP words each), T (2NP, padded), spills: hi words of 2G slots of
+    // up to M words (padded), then one top word per slot
+    static constexpr int OFF_T = LS::OFF_T;
+    static constexpr int OFF_P = (OFF_T + pad_size(2 * NP) + 3) & ~3;
+    static constexpr int SPILL_TOP = (pad_size(2 * G * M) + 3) & ~3;
+    static constexpr int WORDS_RAW = OFF_P + SPILL_TOP + 2 * G;
     // product view: the 32 lanes of a warp read the same offset of 32 records; a stride of
     // 4 (mod 8) words puts each group of 8 lanes' 16-byte accesses on distinct banks
     static constexpr int WORDS = ((WORDS_RAW + 3) / 8) * 8 + 4;
@@ -44,12 +63,12 @@ MPG_DI Views<W> swap_views(uint32_t *smem) {
     Views<W> v;
     const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5);
     v.p.sm = smem + lane * W::WORDS;
-    v.p.pa = v.p.sm + W::LS::OFF_P;
+    v.p.pa = v.p.sm + W::OFF_P;
     v.p.t = warp;
     v.p.gbase = 0;
     const int li = warp * (32 / W::G) + lane / W::G;
     v.l.sm = smem + li * W::WORDS;
-    v.l.pa = v.l.sm + W::LS::OFF_P;
+    v.l.pa = v.l.sm + W::OFF_P;
     v.l.t = lane % W::G;
     v.l.gbase = lane & ~(W::G - 1);
     return v;
@@ -60,6 +79,12 @@ MPG_DI size_t swap_instance() { return (size_t)blockIdx.x * 32 + (threadIdx.x & 
 
 MPG_DI void bsync() { __syncthreads(); }
 
+// spill words of slot s for B-word slots: hi words padded, the top word after them
+template <class W, int B, class S>
+MPG_DI Spill swp_spill(const Grp<S> &g, int s) {
+    return Spill{g.P() + pad32(s * B), g.P() + W::SPILL_TOP + s};
+}
+
 // ------------------------------------------------------------------ product-view phases
 //
 // Thread t of every instance is warp t here, so each slot's blocks form one run of mac_run
@@ -68,52 +93,14 @@ MPG_DI void bsync() { __syncthreads(); }
 // slot sums of T = X * Y: thread t owns slots t (X_j Y_{t-j}, j <= t) and G+t (j > t)
 template <class W>
 MPG_DI void swp_mul_slots(const Grp<typename W::PS> &g, const uint32_t *X, const uint32_t *Y, uint32_t *T) {
-    using S = typename W::PS;
     constexpr int G = W::G, M = W::M, U = run_group<M>();
     const int t = g.t;
     Acc3<M> a;
     acc3_zero<M>(a);
     mac_run<M, U>(a, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
-    flush<M>(a, T + t * M, spill_of<S, M>(g, t));
+    flush<M>(a, T + pad32(t * M), swp_spill<W, M>(g, t));
     mac_run<M, U>(a, X, Y, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
-    park<M>(a, T + (G + t) * M, spill_of<S, M>(g, G + t));
-}
-
-// slot sums of q = T_lo * N' mod R in H-word slots: thread t owns slots t (t+1 blocks) and
-// 2G-1-t (2G-t blocks)
-template <class W>
-MPG_DI void swp_mullo_slots(const Grp<typename W::PS> &g, const uint32_t *X, const uint32_t *Y, uint32_t *Q) {
-    using S = typename W::PS;
-    constexpr int G = W::G, H = W::H, U = run_group<H>();
-    const int t = g.t;
-    Acc3<H> a;
-    acc3_zero<H>(a);
-    mac_run<H, U>(a, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
-    flush<H>(a, Q + t * H, spill_of<S, H>(g, t));
-    mac_run<H, U>(a, X, Y, 2 * G - t, [&](int j, int &u, int &v) { u = j; v = 2 * G - 1 - t - j; });
-    park<H>(a, Q + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
-}
-
-// slot sums of the classical reduction T + q*N over all 2*NP words: T's words of a slot are
-// added before the slot is stored over them
-template <class W>
-MPG_DI void swp_fma_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
-    using S = typename W::PS;
-    constexpr int G = W::G, M = W::M, U = run_group<M>();
-    const int t = g.t;
-    const AddendXform<M> addT{T};
-    Acc3<M> a;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int s = k ? G + t : t;
-        acc3_zero<M>(a);
-        if (k == 0) mac_run<M, U>(a, Qs, Ns, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
-        else mac_run<M, U>(a, Qs, Ns, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
-        uint32_t V[2 * M + 2];
-        acc3_value<M>(V, a);
-        addT(s, V);
-        store_slot<M>(V, T + s * M, spill_of<S, M>(g, s));
-    }
+    park<M>(a, T + pad32((G + t) * M), swp_spill<W, M>(g, G + t));
 }
 
 // V (2M+2 words, below W^(2M+1) / 2) <- 2 V + the squares x_i^2 at columns 2i
@@ -133,16 +120,15 @@ MPG_DI void double_add_diag(uint32_t (&V)[2 * M + 2], const uint32_t (&x)[M]) {
     addc(V[2 * M + 1], 0u);
 }
 
-// Slot sums of T = X^2 in the product view, complete (no transform left for the resolve).
-// Thread t owns slots t and G+t (the cross products X_u X_v, u < v, on those diagonals). The
-// square of block u covers exactly the columns of slot 2u, so the owner of an even slot s
-// (an even t: both of its slots are even) adds X_{s/2}^2 itself: the block's cross terms
-// join the accumulator before the doubling, its squares x_i^2 after it. Every slot sum stays
-// below (G + 2) W^(2M) < W^(2M+1).
+// Slot sums of T = X^2, complete (no transform left for the resolve). Thread t owns slots t
+// and G+t (the cross products X_u X_v, u < v, on those diagonals). The square of block u
+// covers exactly the columns of slot 2u, so the owner of an even slot s (an even t: both of
+// its slots are even) adds X_{s/2}^2 itself: the block's cross terms join the accumulator
+// before the doubling, its squares x_i^2 after it. Every slot sum stays below
+// (G + 2) W^(2M) < W^(2M+1).
 template <class W>
 MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint32_t *T) {
-    using S = typename W::PS;
-    constexpr int G = W::G, M = W::M;
+    constexpr int G = W::G, M = W::M, U = run_group<M>();
     const int t = g.t;
     const bool even = (t & 1) == 0;
     const int nA = (t + 1) >> 1;              // pairs u < v with u + v = t
@@ -152,8 +138,8 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
     for (int k = 0; k < 2; ++k) {
         const int s = k ? G + t : t;
         acc3_zero<M>(a);
-        if (k == 0) mac_run<M, run_group<M>()>(a, X, X, nA, [&](int j, int &u, int &v) { u = j; v = t - j; });
-        else mac_run<M, run_group<M>()>(a, X, X, nB, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
+        if (k == 0) mac_run<M, U>(a, X, X, nA, [&](int j, int &u, int &v) { u = j; v = t - j; });
+        else mac_run<M, U>(a, X, X, nB, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
         uint32_t x[M];
         if (even) {   // warp-uniform
             lds<M>(x, X + (s >> 1) * M);
@@ -164,7 +150,47 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
         uint32_t V[2 * M + 2];
         acc3_value<M>(V, a);
         double_add_diag<M>(V, x);
-        store_slot<M>(V, T + s * M, spill_of<S, M>(g, s));
+        store_slot<M>(V, T + pad32(s * M), swp_spill<W, M>(g, s));
+    }
+}
+
+// slot sums of q = T_lo * N' mod R in H-word slots: thread t owns slots t (t+1 blocks) and
+// 2G-1-t (2G-t blocks); T is read through its padding
+template <class W>
+MPG_DI void swp_mullo_slots(const Grp<typename W::PS> &g, const uint32_t *T, const uint32_t *NI, uint32_t *Q) {
+    constexpr int G = W::G, H = W::H, U = run_group<H>();
+    const int t = g.t;
+    Acc3<H> a;
+    acc3_zero<H>(a);
+    mac_run<H, U>(a, T, NI, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; }, PadMap{});
+    flush<H>(a, Q + t * H, swp_spill<W, H>(g, t));
+    mac_run<H, U>(a, T, NI, 2 * G - t, [&](int j, int &u, int &v) { u = j; v = 2 * G - 1 - t - j; }, PadMap{});
+    park<H>(a, Q + (2 * G - 1 - t) * H, swp_spill<W, H>(g, 2 * G - 1 - t));
+}
+
+// slot sums of the classical reduction T + q*N over all 2*NP words: T's words of a slot are
+// added before the slot is stored over them
+template <class W>
+MPG_DI void swp_fma_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *T) {
+    constexpr int G = W::G, M = W::M, U = run_group<M>();
+    const int t = g.t;
+    Acc3<M> a;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = k ? G + t : t;
+        acc3_zero<M>(a);
+        if (k == 0) mac_run<M, U>(a, Qs, Ns, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
+        else mac_run<M, U>(a, Qs, Ns, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
+        uint32_t V[2 * M + 2], d[M];
+        acc3_value<M>(V, a);
+        lds<M>(d, T + pad32(s * M));
+        add_cc(V[0], d[0]);
+#pragma unroll
+        for (int j = 1; j < M; ++j) addc_cc(V[j], d[j]);
+#pragma unroll
+        for (int j = M; j < 2 * M + 1; ++j) addc_cc(V[j], 0u);
+        addc(V[2 * M + 1], 0u);
+        store_slot<M>(V, T + pad32(s * M), swp_spill<W, M>(g, s));
     }
 }
 
@@ -228,8 +254,7 @@ MPG_DI void zacc_value(uint32_t (&Z)[H + 3], const ZAcc<H> &z) {
 // of the Thm. 2 boundary sum parked in T's low half (dead once q is formed; word NP-1 kept).
 template <class W>
 MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, const uint32_t *Ns, uint32_t *C,
-                            const uint32_t *Thi) {
-    using S = typename W::PS;
+                            const uint32_t *T) {
     constexpr int G = W::G, H = W::H, NP = W::NP;
     const int t = g.t;
     {
@@ -263,25 +288,212 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
 #pragma unroll
         for (int k = 0; k < H + 3; ++k) zs[k] = Z[k];
     }
-    const AddendXform<H> addT{Thi};
-    Acc3<H> a;
-    acc3_zero<H>(a);
     constexpr int U = run_group<H>();
-    mac_run<H, U>(a, Qs, Ns, 2 * G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; });
-    {
-        uint32_t V[2 * H + 2];
+    Acc3<H> a;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = k ? 2 * G - 1 - t : t;
+        acc3_zero<H>(a);
+        if (k == 0) mac_run<H, U>(a, Qs, Ns, 2 * G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = 2 * G - 1 - j; });
+        else mac_run<H, U>(a, Qs, Ns, t, [&](int j, int &u, int &v) { u = 2 * G - t + j; v = 2 * G - 1 - j; });
+        uint32_t V[2 * H + 2], d[H];
         acc3_value<H>(V, a);
-        addT(t, V);
-        store_slot<H>(V, C + t * H, spill_of<S, H>(g, t));
+        lds<H>(d, T + pad32(NP + s * H));
+        add_cc(V[0], d[0]);
+#pragma unroll
+        for (int j = 1; j < H; ++j) addc_cc(V[j], d[j]);
+#pragma unroll
+        for (int j = H; j < 2 * H + 1; ++j) addc_cc(V[j], 0u);
+        addc(V[2 * H + 1], 0u);
+        store_slot<H>(V, C + s * H, swp_spill<W, H>(g, s));
     }
-    acc3_zero<H>(a);
-    mac_run<H, U>(a, Qs, Ns, t, [&](int k, int &u, int &v) { u = 2 * G - t + k; v = 2 * G - 1 - k; });
-    {
-        uint32_t V[2 * H + 2];
-        acc3_value<H>(V, a);
-        addT(2 * G - 1 - t, V);
-        store_slot<H>(V, C + (2 * G - 1 - t) * H, spill_of<S, H>(g, 2 * G - 1 - t));
+}
+
+// ------------------------------------------------------------------ carry-view phases
+
+// Resolve the stored slot sums (low words at OUT through om, spills in the padded area) into
+// final words: add each predecessor's spill, pass the overflow word on with a shuffle, and
+// resolve the remaining one-bit carries of the group with ballots (carry-lookahead). The
+// final words of this thread's two slots are left in fin[k] (slot slot_of<G, PAT>(t, k)),
+// not stored; only their owner reads a slot's low words, so the caller may store them at
+// once. Returns the low word of everything above the last slot.
+template <class W, int B, int PAT, class OM>
+MPG_DI uint32_t cv_resolve(const Grp<typename W::LS> &g, const uint32_t (&in0)[B + 2], const uint32_t *OUT, const OM &om,
+                           uint32_t (&fin)[2][B]) {
+    constexpr int G = W::G, NSLOT = 2 * G;
+    uint32_t top = 0u;
+    uint32_t ov[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        uint32_t lo[B];
+        lds<B>(lo, OUT + om(s * B));
+        if (s == NSLOT - 1) top = g.P()[pad32(s * B)];   // word B of the last slot's sum
+        uint32_t x[B + 2];
+        if (s == 0) {
+#pragma unroll
+            for (int j = 0; j < B + 2; ++j) x[j] = in0[j];
+        } else {
+            uint32_t h[B];
+            lds<B>(h, g.P() + pad32((s - 1) * B));
+#pragma unroll
+            for (int j = 0; j < B; ++j) x[j] = h[j];
+            x[B] = g.P()[W::SPILL_TOP + s - 1];
+            x[B + 1] = 0u;
+        }
+        add_cc(x[0], lo[0]);
+#pragma unroll
+        for (int j = 1; j < B; ++j) addc_cc(x[j], lo[j]);
+        addc_cc(x[B], 0u);
+        addc(x[B + 1], 0u);
+#pragma unroll
+        for (int j = 0; j < B; ++j) fin[k][j] = x[j];
+        ov[k][0] = x[B];
+        ov[k][1] = x[B + 1];
+        if (s == NSLOT - 1) top += x[B];
     }
+    uint32_t oin[2][2];
+    pred_overflow<G, PAT>(g.t, g.gbase, ov[0], ov[1], oin[0], oin[1]);
+    uint32_t cgen[2], cprop[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        add_cc(fin[k][0], oin[k][0]);
+        addc_cc(fin[k][1], oin[k][1]);
+#pragma unroll
+        for (int j = 2; j < B; ++j) addc_cc(fin[k][j], 0u);
+        cgen[k] = addc_get();
+        uint32_t all = fin[k][0];
+#pragma unroll
+        for (int j = 1; j < B; ++j) all &= fin[k][j];
+        cprop[k] = (all == 0xffffffffu) ? 1u : 0u;
+    }
+    const bool pr[4] = {cgen[0] != 0u, cprop[0] != 0u, cgen[1] != 0u, cprop[1] != 0u};
+    uint32_t mk[4];
+    g.template bits<4>(pr, mk);
+    const uint64_t Gm = slot_mask<G, PAT>(mk[0], mk[2]);
+    const uint64_t Pm = slot_mask<G, PAT>(mk[1], mk[3]);
+    const uint64_t cin = (Pm + (Gm << 1)) ^ Pm;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) add_word<B>(fin[k], (uint32_t)(cin >> slot_of<G, PAT>(g.t, k)) & 1u);
+    constexpr int owner = (PAT == PAT_ZIGZAG) ? 0 : G - 1;
+    top = g.bcast(top, owner);
+    return top + ((uint32_t)(cin >> NSLOT) & 1u);
+}
+
+// T resolved in place, and c_add = [T mod R != 0], low_zero = [T mod W^(NP-1) == 0] for the
+// whole group from the resolved words (slot t, this thread's first, is T's words tM..tM+M-1)
+template <class W>
+MPG_DI void cv_resolve_T(const Grp<typename W::LS> &g, uint32_t &c_add, uint32_t &low_zero) {
+    constexpr int M = W::M, NP = W::NP, G = W::G;
+    uint32_t in0[M + 2], fin[2][M];
+    zero<M + 2>(in0);
+    cv_resolve<W, M, PAT_SEQ>(g, in0, g.T(), PadMap{}, fin);
+    uint32_t nz_all = 0u, nz_low = 0u;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        nz_all |= fin[0][j];
+        if (g.t * M + j < NP - 1) nz_low |= fin[0][j];
+    }
+    const bool pr[2] = {nz_all != 0u, nz_low != 0u};
+    uint32_t mk[2];
+    g.template bits<2>(pr, mk);
+    c_add = mk[0] ? 1u : 0u;
+    low_zero = mk[1] ? 0u : 1u;
+    sts<M>(g.T() + pad32(g.t * M), fin[0]);
+    sts<M>(g.T() + pad32((G + g.t) * M), fin[1]);
+}
+
+// q resolved in place (H-word slots in Y)
+template <class W>
+MPG_DI void cv_resolve_q(const Grp<typename W::LS> &g) {
+    constexpr int H = W::H, G = W::G;
+    uint32_t in0[H + 2], fin[2][H];
+    zero<H + 2>(in0);
+    cv_resolve<W, H, PAT_ZIGZAG>(g, in0, g.Q(), IdMap{}, fin);
+    sts<H>(g.Q() + g.t * H, fin[0]);
+    sts<H>(g.Q() + (2 * G - 1 - g.t) * H, fin[1]);
+}
+
+// OUT segments = (top*R + C >= N) ? C - N : C, constant time, for two segments per thread of
+// K words in slot order PAT; borrows cross the group with the same lookahead as carries
+template <class W, int K, int PAT>
+MPG_DI void cv_cond_sub(const Grp<typename W::LS> &g, uint32_t (&c)[2][K], uint32_t top, const uint32_t *Ns, uint32_t *OUT) {
+    constexpr int G = W::G, NSEG = (PAT == PAT_ONE) ? G : 2 * G;
+    constexpr int NK = (PAT == PAT_ONE) ? 1 : 2;
+    uint32_t d[2][K];
+    bool pr[4] = {false, false, false, false};
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        uint32_t n[K];
+        lds<K>(n, Ns + s * K);
+        uint32_t eq = 0u;
+#pragma unroll
+        for (int j = 0; j < K; ++j) { d[k][j] = c[k][j]; eq |= c[k][j] ^ n[j]; }
+        pr[2 * k] = sub_n<K>(d[k], n) != 0u;
+        pr[2 * k + 1] = eq == 0u;
+    }
+    uint32_t mk[4];
+    g.template bits<4>(pr, mk);
+    const uint64_t Gm = slot_mask<G, PAT>(mk[0], mk[2]);
+    const uint64_t Pm = slot_mask<G, PAT>(mk[1], mk[3]);
+    const uint64_t bin = (Pm + (Gm << 1)) ^ Pm;
+    const uint32_t borrow_out = (uint32_t)(bin >> NSEG) & 1u;
+    const uint32_t msk = 0u - (top | (borrow_out ^ 1u));
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int s = slot_of<G, PAT>(g.t, k);
+        sub_word<K>(d[k], (uint32_t)(bin >> s) & 1u);
+#pragma unroll
+        for (int j = 0; j < K; ++j) d[k][j] = (d[k][j] & msk) | (c[k][j] & ~msk);
+        sts<K>(OUT + s * K, d[k]);
+    }
+}
+
+// truncated high half: group sum of the boundary terms, carry recovery from word NP-1 of -T
+// (Thm. 1/2), C = floor(T/R) + floor(qN/R) + c_add resolved, then the final subtraction on the
+// resolved words (skipped when lazy); result in X
+template <class W>
+MPG_DI void cv_resolve_hi(const Grp<typename W::LS> &g, uint32_t c_add, uint32_t low_zero, bool lazy) {
+    constexpr int H = W::H, G = W::G, NP = W::NP;
+    uint32_t Z[H + 3];
+    lds<H + 3>(Z, g.T() + g.t * (H + 3));
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {   // sum over the instance's G lanes
+        uint32_t o[H + 3];
+#pragma unroll
+        for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
+        add_n<H + 3>(Z, o);
+    }
+    // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
+    const uint32_t L = ~g.T()[pad32(NP - 1)] + low_zero;
+    const uint32_t extra = (uint32_t)(((uint64_t)L - (uint64_t)Z[0]) >> 63);   // [L < Z[0]]
+    uint32_t in0[H + 2], fin[2][H];
+#pragma unroll
+    for (int j = 0; j < H + 2; ++j) in0[j] = Z[1 + j];
+    add_word<H + 2>(in0, extra + c_add);
+    const uint32_t top = cv_resolve<W, H, PAT_ZIGZAG>(g, in0, g.X(), IdMap{}, fin);
+    if (lazy) {
+        sts<H>(g.X() + g.t * H, fin[0]);
+        sts<H>(g.X() + (2 * G - 1 - g.t) * H, fin[1]);
+    } else {
+        cv_cond_sub<W, H, PAT_ZIGZAG>(g, fin, top, g.N(), g.X());
+    }
+}
+
+// classical: T + qN resolved; C = its high half (slot G+t of thread t is C's words tM ..),
+// then the final subtraction (skipped when lazy); result in X
+template <class W>
+MPG_DI void cv_resolve_fma(const Grp<typename W::LS> &g, bool lazy) {
+    constexpr int M = W::M;
+    uint32_t in0[M + 2], fin[2][M];
+    zero<M + 2>(in0);
+    const uint32_t top = cv_resolve<W, M, PAT_SEQ>(g, in0, g.T(), PadMap{}, fin);
+    uint32_t c[2][M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) { c[0][j] = fin[1][j]; c[1][j] = 0u; }
+    if (lazy) sts<M>(g.X() + g.t * M, c[0]);
+    else cv_cond_sub<W, M, PAT_ONE>(g, c, top, g.N(), g.X());
 }
 
 // X <- X * Y * R^-1 mod N, or X^2 * R^-1 mod N (Y then unused); Y holds q afterwards.
@@ -289,63 +501,32 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
 // result behind a block barrier. lazy: no final subtraction (results < 2N when 4N <= R).
 template <class W, int RED>
 MPG_DI void swap_mont(const Views<W> &v, bool square, bool lazy) {
-    using PS = typename W::PS;
-    using LS = typename W::LS;
-    constexpr int M = W::M, H = W::H, NP = W::NP, G = W::G;
-    const Grp<PS> &gp = v.p;
-    const Grp<LS> &gl = v.l;
+    const auto &gp = v.p;
+    const auto &gl = v.l;
     // 1. T = X * Y or X^2 (slot sums in the product view, carries in the carry view)
     if (square) swp_sqr_slots<W>(gp, gp.X(), gp.T());
     else swp_mul_slots<W>(gp, gp.X(), gp.Y(), gp.T());
     bsync();
-    {
-        uint32_t in0[M + 2];
-        zero<M + 2>(in0);
-        resolve<LS, M, PAT_SEQ>(gl, in0, NoXform{}, gl.T());
-    }
     uint32_t c_add, low_zero;
-    reduce_flags<LS>(gl, gl.T(), c_add, low_zero);
+    cv_resolve_T<W>(gl, c_add, low_zero);
     bsync();
     // 2. q = T_lo * N' mod R
     swp_mullo_slots<W>(gp, gp.T(), gp.NI(), gp.Q());
     bsync();
-    {
-        uint32_t in0[H + 2];
-        zero<H + 2>(in0);
-        resolve<LS, H, PAT_ZIGZAG>(gl, in0, NoXform{}, gl.Q());
-    }
+    cv_resolve_q<W>(gl);
     bsync();
     if constexpr (RED == 0) {
         // 3. C = floor(T/R) + floor(qN/R) + c_add from the high half of qN (Thm. 2)
-        swp_mulhi_slots<W>(gp, gp.Q(), gp.N(), gp.X(), gp.T() + NP);
+        swp_mulhi_slots<W>(gp, gp.Q(), gp.N(), gp.X(), gp.T());
         bsync();
-        uint32_t Z[H + 3];
-        lds<H + 3>(Z, gl.T() + gl.t * (H + 3));
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {   // sum over the instance's G lanes
-            uint32_t o[H + 3];
-#pragma unroll
-            for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
-            add_n<H + 3>(Z, o);
-        }
-        const uint32_t carry = mulhi_resolve<LS>(gl, Z, gl.T(), c_add, low_zero, gl.X(), NoXform{});
-        if (!lazy) cond_sub<LS>(gl, gl.X(), carry, gl.N(), gl.X());
+        cv_resolve_hi<W>(gl, c_add, low_zero, lazy);
     } else {
         // 3. classical: T + q*N over all words, C = its high half
         (void)c_add;
         (void)low_zero;
         swp_fma_slots<W>(gp, gp.Q(), gp.N(), gp.T());
         bsync();
-        uint32_t in0[M + 2];
-        zero<M + 2>(in0);
-        const uint32_t carry = resolve<LS, M, PAT_SEQ>(gl, in0, NoXform{}, gl.T());
-        if (!lazy) {
-            cond_sub<LS>(gl, gl.T() + NP, carry, gl.N(), gl.X());
-        } else {
-            uint32_t x[M];
-            lds<M>(x, gl.T() + NP + gl.t * M);
-            sts<M>(gl.X() + gl.t * M, x);
-        }
+        cv_resolve_fma<W>(gl, lazy);
     }
     bsync();
 }
