@@ -23,12 +23,15 @@
 namespace mpg {
 
 // word offset of logical word i of a padded array (T, slot spills): four pad words follow
-// every 32 words. Blocks of 4 or 8 words never straddle a row, so they stay contiguous.
-MPG_DI int pad32(int i) { return i + ((i >> 5) << 2); }
-constexpr int pad_size(int n) { return n ? (n - 1) + (((n - 1) >> 5) << 2) + 1 : 0; }
+// every 32 words. Blocks of 4, 8 or 16 words never straddle a row, so they stay contiguous.
+// Shapes whose M is not a multiple of 8 do not pad (P = false).
+template <bool P = true>
+MPG_DI int pad32(int i) { return P ? i + ((i >> 5) << 2) : i; }
+constexpr int pad_size(int n, bool p = true) { return !p ? n : n ? (n - 1) + (((n - 1) >> 5) << 2) + 1 : 0; }
 
+template <bool P>
 struct PadMap {
-    MPG_DI int operator()(int i) const { return pad32(i); }
+    MPG_DI int operator()(int i) const { return pad32<P>(i); }
 };
 
 template <int G_, int M_>
@@ -38,13 +41,15 @@ struct Swap {
     static constexpr int G = G_, M = M_, NP = G_ * M_, H = M_ / 2;
     static constexpr int TPB = 32 * G_;   // 32 instances per block
     static_assert(LS::MONT_OK, "Montgomery needs an even M >= 4");
-    static_assert(M_ % 4 == 0 && 32 % M_ == 0 || M_ == 16, "padded rows hold whole blocks");
     static_assert(PS::OFF_T == LS::OFF_T, "one record layout for both views");
+    static_assert(32 % G_ == 0, "the G threads of an instance share a warp in the carry view");
+    // pad T and the spills where a thread's M-word slots repeat the bank pattern (M = 8, 16)
+    static constexpr bool PAD = (M_ % 8 == 0);
     // record: X, Y (q), N, N' (NP words each), T (2NP, padded), spills: hi words of 2G slots of
     // up to M words (padded), then one top word per slot
     static constexpr int OFF_T = LS::OFF_T;
-    static constexpr int OFF_P = (OFF_T + pad_size(2 * NP) + 3) & ~3;
-    static constexpr int SPILL_TOP = (pad_size(2 * G * M) + 3) & ~3;
+    static constexpr int OFF_P = (OFF_T + pad_size(2 * NP, PAD) + 3) & ~3;
+    static constexpr int SPILL_TOP = (pad_size(2 * G * M, PAD) + 3) & ~3;
     static constexpr int WORDS_RAW = OFF_P + SPILL_TOP + 2 * G;
     // product view: the 32 lanes of a warp read the same offset of 32 records; a stride of
     // 4 (mod 8) words puts each group of 8 lanes' 16-byte accesses on distinct banks
@@ -82,7 +87,7 @@ MPG_DI void bsync() { __syncthreads(); }
 // spill words of slot s for B-word slots: hi words padded, the top word after them
 template <class W, int B, class S>
 MPG_DI Spill swp_spill(const Grp<S> &g, int s) {
-    return Spill{g.P() + pad32(s * B), g.P() + W::SPILL_TOP + s};
+    return Spill{g.P() + pad32<W::PAD>(s * B), g.P() + W::SPILL_TOP + s};
 }
 
 // ------------------------------------------------------------------ product-view phases
@@ -98,9 +103,9 @@ MPG_DI void swp_mul_slots(const Grp<typename W::PS> &g, const uint32_t *X, const
     Acc3<M> a;
     acc3_zero<M>(a);
     mac_run<M, U>(a, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
-    flush<M>(a, T + pad32(t * M), swp_spill<W, M>(g, t));
+    flush<M>(a, T + pad32<W::PAD>(t * M), swp_spill<W, M>(g, t));
     mac_run<M, U>(a, X, Y, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
-    park<M>(a, T + pad32((G + t) * M), swp_spill<W, M>(g, G + t));
+    park<M>(a, T + pad32<W::PAD>((G + t) * M), swp_spill<W, M>(g, G + t));
 }
 
 // V (2M+2 words, below W^(2M+1) / 2) <- 2 V + the squares x_i^2 at columns 2i
@@ -150,7 +155,7 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
         uint32_t V[2 * M + 2];
         acc3_value<M>(V, a);
         double_add_diag<M>(V, x);
-        store_slot<M>(V, T + pad32(s * M), swp_spill<W, M>(g, s));
+        store_slot<M>(V, T + pad32<W::PAD>(s * M), swp_spill<W, M>(g, s));
     }
 }
 
@@ -162,9 +167,9 @@ MPG_DI void swp_mullo_slots(const Grp<typename W::PS> &g, const uint32_t *T, con
     const int t = g.t;
     Acc3<H> a;
     acc3_zero<H>(a);
-    mac_run<H, U>(a, T, NI, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; }, PadMap{});
+    mac_run<H, U>(a, T, NI, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; }, PadMap<W::PAD>{});
     flush<H>(a, Q + t * H, swp_spill<W, H>(g, t));
-    mac_run<H, U>(a, T, NI, 2 * G - t, [&](int j, int &u, int &v) { u = j; v = 2 * G - 1 - t - j; }, PadMap{});
+    mac_run<H, U>(a, T, NI, 2 * G - t, [&](int j, int &u, int &v) { u = j; v = 2 * G - 1 - t - j; }, PadMap<W::PAD>{});
     park<H>(a, Q + (2 * G - 1 - t) * H, swp_spill<W, H>(g, 2 * G - 1 - t));
 }
 
@@ -183,14 +188,14 @@ MPG_DI void swp_fma_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, cons
         else mac_run<M, U>(a, Qs, Ns, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
         uint32_t V[2 * M + 2], d[M];
         acc3_value<M>(V, a);
-        lds<M>(d, T + pad32(s * M));
+        lds<M>(d, T + pad32<W::PAD>(s * M));
         add_cc(V[0], d[0]);
 #pragma unroll
         for (int j = 1; j < M; ++j) addc_cc(V[j], d[j]);
 #pragma unroll
         for (int j = M; j < 2 * M + 1; ++j) addc_cc(V[j], 0u);
         addc(V[2 * M + 1], 0u);
-        store_slot<M>(V, T + pad32(s * M), swp_spill<W, M>(g, s));
+        store_slot<M>(V, T + pad32<W::PAD>(s * M), swp_spill<W, M>(g, s));
     }
 }
 
@@ -298,7 +303,7 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
         else mac_run<H, U>(a, Qs, Ns, t, [&](int j, int &u, int &v) { u = 2 * G - t + j; v = 2 * G - 1 - j; });
         uint32_t V[2 * H + 2], d[H];
         acc3_value<H>(V, a);
-        lds<H>(d, T + pad32(NP + s * H));
+        lds<H>(d, T + pad32<W::PAD>(NP + s * H));
         add_cc(V[0], d[0]);
 #pragma unroll
         for (int j = 1; j < H; ++j) addc_cc(V[j], d[j]);
@@ -328,14 +333,14 @@ MPG_DI uint32_t cv_resolve(const Grp<typename W::LS> &g, const uint32_t (&in0)[B
         const int s = slot_of<G, PAT>(g.t, k);
         uint32_t lo[B];
         lds<B>(lo, OUT + om(s * B));
-        if (s == NSLOT - 1) top = g.P()[pad32(s * B)];   // word B of the last slot's sum
+        if (s == NSLOT - 1) top = g.P()[pad32<W::PAD>(s * B)];   // word B of the last slot's sum
         uint32_t x[B + 2];
         if (s == 0) {
 #pragma unroll
             for (int j = 0; j < B + 2; ++j) x[j] = in0[j];
         } else {
             uint32_t h[B];
-            lds<B>(h, g.P() + pad32((s - 1) * B));
+            lds<B>(h, g.P() + pad32<W::PAD>((s - 1) * B));
 #pragma unroll
             for (int j = 0; j < B; ++j) x[j] = h[j];
             x[B] = g.P()[W::SPILL_TOP + s - 1];
@@ -387,7 +392,7 @@ MPG_DI void cv_resolve_T(const Grp<typename W::LS> &g, uint32_t &c_add, uint32_t
     constexpr int M = W::M, NP = W::NP, G = W::G;
     uint32_t in0[M + 2], fin[2][M];
     zero<M + 2>(in0);
-    cv_resolve<W, M, PAT_SEQ>(g, in0, g.T(), PadMap{}, fin);
+    cv_resolve<W, M, PAT_SEQ>(g, in0, g.T(), PadMap<W::PAD>{}, fin);
     uint32_t nz_all = 0u, nz_low = 0u;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -399,8 +404,8 @@ MPG_DI void cv_resolve_T(const Grp<typename W::LS> &g, uint32_t &c_add, uint32_t
     g.template bits<2>(pr, mk);
     c_add = mk[0] ? 1u : 0u;
     low_zero = mk[1] ? 0u : 1u;
-    sts<M>(g.T() + pad32(g.t * M), fin[0]);
-    sts<M>(g.T() + pad32((G + g.t) * M), fin[1]);
+    sts<M>(g.T() + pad32<W::PAD>(g.t * M), fin[0]);
+    sts<M>(g.T() + pad32<W::PAD>((G + g.t) * M), fin[1]);
 }
 
 // q resolved in place (H-word slots in Y)
@@ -466,7 +471,7 @@ MPG_DI void cv_resolve_hi(const Grp<typename W::LS> &g, uint32_t c_add, uint32_t
         add_n<H + 3>(Z, o);
     }
     // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
-    const uint32_t L = ~g.T()[pad32(NP - 1)] + low_zero;
+    const uint32_t L = ~g.T()[pad32<W::PAD>(NP - 1)] + low_zero;
     const uint32_t extra = (uint32_t)(((uint64_t)L - (uint64_t)Z[0]) >> 63);   // [L < Z[0]]
     uint32_t in0[H + 2], fin[2][H];
 #pragma unroll
@@ -488,7 +493,7 @@ MPG_DI void cv_resolve_fma(const Grp<typename W::LS> &g, bool lazy) {
     constexpr int M = W::M;
     uint32_t in0[M + 2], fin[2][M];
     zero<M + 2>(in0);
-    const uint32_t top = cv_resolve<W, M, PAT_SEQ>(g, in0, g.T(), PadMap{}, fin);
+    const uint32_t top = cv_resolve<W, M, PAT_SEQ>(g, in0, g.T(), PadMap<W::PAD>{}, fin);
     uint32_t c[2][M];
 #pragma unroll
     for (int j = 0; j < M; ++j) { c[0][j] = fin[1][j]; c[1][j] = 0u; }
