@@ -167,17 +167,20 @@ int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_t *exp, uin
                      void *workspace, size_t workspace_bytes, void *stream);
 
 /*
- * Mixed-size batches in one persistent launch (pattern (2) of the serving/batching
- * use of Alg. 7): each job is one context's batch of exponentiations, with its own
- * operand size, exponent length and window (0 = tuned), run with the group shape
- * selected for its size. Jobs of up to 4096 bits (padded sizes 512/1024/2048/3072/
- * 4096 bits), at most 16 per call. All jobs run in
- * ONE kernel launch: blocks pull tiles of instances from an atomic counter, the
- * costliest job first, so the launch can be captured in a CUDA graph together with
- * its input copies. Results equal those of modexp_consttime on each job.
+ * Mixed-size batches (pattern (2) of the serving/batching use of Alg. 7): each job is
+ * one context's batch of exponentiations, with its own operand size, exponent length
+ * and window (0 = tuned), run with the kernel modexp_consttime would use for it (the
+ * shape selected for its size class). Any size the library supports, at most 16 jobs
+ * per call. The jobs are independent: the call forks them onto parallel streams of the
+ * library, the costliest job first, and joins them back to `stream` with events, so the
+ * GPU fills the last partial wave of one job with blocks of the next, and the call
+ * (fork, launches, join) can be captured in a CUDA graph together with its copies.
+ * Results equal those of modexp_consttime on each job.
  * red: MP_RED_TRUNCATED, MP_RED_FULL or MP_RED_CIOS, for every job of the call.
  * workspace: at least modexp_mixed_workspace_bytes(jobs, njobs) bytes, 256-byte
- * aligned (window tables plus the tile counter, which the call resets on `stream`).
+ * aligned (the window tables of the jobs that are not fixed-base).
+ * The first call on a device creates that device's streams and events (outside any
+ * stream capture); calls from several host threads are serialised around the fork.
  */
 typedef struct {
     uint32_t *y;            /* results, n words per instance, context layout */

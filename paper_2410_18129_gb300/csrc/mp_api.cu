@@ -449,6 +449,8 @@ static uint32_t tuned_window(uint32_t bits) {
 
 uint32_t mpg::default_window(uint32_t bits) { return tuned_window(bits); }
 
+const ShapeOps *mpg::shape_for_red_np(uint32_t np, int red) { return shape_for_red(np, red); }
+
 extern "C" int mp_shape_candidates(uint32_t bits, int *G, int *M, int max) {
     if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
     const SizeClass *c = class_for(words_for(bits));

@@ -21,4 +21,7 @@ namespace mpg {
 void ctx_args(KArgs &A, const mont_ctx *c);
 // window used when the caller passes window = 0
 uint32_t default_window(uint32_t bits);
+// kernels of the size class of np words for reduction red (the selected shape; a lane-mapped one
+// for the word-serial reduction), or null
+const ShapeOps *shape_for_red_np(uint32_t np, int red);
 }  // namespace mpg

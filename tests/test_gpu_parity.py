@@ -408,7 +408,7 @@ def test_truncated_karatsuba_unavailable(mp):
         ctx.free()
 
 
-# ------------------------------------------------------------------ mixed sizes, one persistent launch
+# ------------------------------------------------------------------ mixed sizes in one call
 
 def _mixed_jobs(mp, specs, layout):
     jobs, batches, outs = [], [], []
@@ -423,12 +423,14 @@ def _mixed_jobs(mp, specs, layout):
 
 
 @pytest.mark.parametrize("layout", [IM, IL])
-def test_mixed_persistent_matches_per_size(mp, layout):
+def test_mixed_matches_per_size(mp, layout):
+    """Every job of a mixed call (all size classes, ragged batches, short exponents) equals
+    modexp_consttime on that job alone, and sampled instances equal the oracle."""
     specs = [(2048, 70, 2048, 5, 1), (1024, 133, 1024, 4, 2), (3072, 21, 3072, 5, 3), (4096, 17, 4096, 6, 4),
-             (512, 40, 300, 3, 5), (1000, 9, 64, 0, 6)]
+             (512, 40, 300, 3, 5), (1000, 9, 64, 0, 6), (4108, 5, 128, 4, 7), (4607, 3, 96, 5, 8)]
     jobs, batches, outs = _mixed_jobs(mp, specs, layout)
     ws = mp.mixed_workspace(jobs)
-    for red in (0, 1):
+    for red in (0, 1, 2):
         for Y in outs:
             Y.zero_()
         mp.modexp_consttime_mixed(jobs, red, ws)
@@ -437,23 +439,29 @@ def test_mixed_persistent_matches_per_size(mp, layout):
             Z = torch.zeros_like(Y)
             mp.modexp_consttime(Z, A, E, ebits, ctx, window, red)
             got = host(mp, Y, b.batch, b.n, layout)
-            assert_equal(got, host(mp, Z, b.batch, b.n, layout), f"mixed vs one-size {b.bits}")
+            assert_equal(got, host(mp, Z, b.batch, b.n, layout), f"mixed vs one-size {b.bits} red={red}")
             idx = np.arange(0, b.batch, max(1, b.batch // 5))
             want = oracle.modexp(b.a[idx], b.e[idx], ebits, b.N[idx])
-            assert_equal(got[idx], want, f"mixed vs oracle {b.bits}")
+            assert_equal(got[idx], want, f"mixed vs oracle {b.bits} red={red}")
 
 
-def test_mixed_rejects_unsupported(mp):
-    """Sizes above 4096 bits have no shape in the persistent kernel: rejected before any launch."""
-    b = si.make_batch(0, "mixed", 4, 4108, ebits=8, sub=9)
-    ctx = mp.MontCtx(dev(mp, b.N, IM), 4, 4108, IM)
-    Y = out_tensor(mp, 4, b.n, IM)
-    job = [(Y, dev(mp, b.a, IM), dev(mp, b.e, IM), 8, ctx, 5)]
-    assert mp.modexp_mixed_workspace_bytes(job) == 0
-    ws = torch.empty(1 << 20, dtype=torch.int32, device="cuda")
+def test_mixed_many_jobs_and_limits(mp):
+    """16 jobs (more than the call's parallel streams) in one call, twice in a row; a 17th job
+    is rejected before any launch."""
+    specs = [((1024, 2048, 512, 3072)[i % 4], 5 + i, 64, 0, 20 + i) for i in range(16)]
+    jobs, batches, outs = _mixed_jobs(mp, specs, IL)
+    ws = mp.mixed_workspace(jobs)
+    for _ in range(2):
+        for Y in outs:
+            Y.zero_()
+        mp.modexp_consttime_mixed(jobs, 0, ws)
+        torch.cuda.synchronize()
+        for (Y, A, E, ebits, ctx, window), b in zip(jobs, batches):
+            want = oracle.modexp(b.a, b.e, ebits, b.N)
+            assert_equal(host(mp, Y, b.batch, b.n, IL), want, f"16-job call, {b.bits} bits")
     with pytest.raises(mp.MpError) as e:
-        mp.modexp_consttime_mixed(job, 0, ws)
-    assert e.value.status == -7
+        mp.modexp_consttime_mixed(jobs + jobs[:1], 0, ws)
+    assert e.value.status == -2
 
 
 def test_tuning_round_trip(mp):
