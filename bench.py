@@ -12,6 +12,15 @@ Prints one JSON line (rank 0). Under torchrun every rank runs its own batch
 (weak scaling, no collective on the data path); `value` = all instances of all
 ranks / the slowest rank's time. `--impl reference` times the CPU oracle (plain
 left-to-right square-and-multiply) on a bounded sample of the same workload.
+
+Beside the headline the default line carries, each with its fraction of the
+measured IMAD roofline: the classical (Alg. 5) and word-serial (Alg. 4)
+reductions on the same batch, the batched form (`mixed`: 100,000 exponentiations
+of four sizes in one mixed call, plain one-launch-per-size and CUDA-graph end to
+end beside it) and the served form (`serving`: Poisson arrivals at 1e4, 1e5 and
+1e6 requests/s over a resident pool, p50/p99 latency, plain path beside it).
+Every instance of the headline run is checked against the oracle on the host
+cores while the GPU measures those forms (`parity`).
 """
 from __future__ import annotations
 
@@ -178,6 +187,10 @@ def main():
     ap.add_argument("--algo", default="auto", choices=["auto", "karatsuba"],
                     help="product form of the timed modexp steps with --quick: karatsuba runs every "
                          "Montgomery product in the truncated Karatsuba form")
+    ap.add_argument("--sampled-parity", action="store_true",
+                    help="check 24 sampled instances against the oracle instead of all of them")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave out the mixed-size and serving forms of the default line")
     ap.add_argument("--workload", default="batch_2048", choices=["batch_2048", "batch_4096", "mixed", "serving"],
                     help="batch_2048: the headline line; batch_4096: 4096-bit products (schoolbook vs "
                          "Karatsuba, 4108/4154 edges), Montgomery and w=6 modexp")
@@ -336,25 +349,13 @@ def main():
     h2d = (hA.numel() + hE.numel()) * 4
     d2h = hY.numel() * 4
 
-    # sampled parity of the timed configuration (bit-exact vs the oracle)
-    parity = None
-    if rank == 0:
-        import oracle
-        idx = np.linspace(0, B - 1, 24).astype(int)
-        got = mp.deinterleave(mp.to_host(Y), B, n)[idx]
-        want = oracle.modexp(b.a[idx], b.e[idx], ebits, b.N[idx])
-        parity = {"sampled": int(idx.size), "mismatches": int((got != want).any(axis=1).sum())}
+    got_all = mp.deinterleave(mp.to_host(Y), B, n)   # this run's results, every instance
 
     traffic = recorded_traffic("k_modexp_2048_w5", B)
     imad = modexp_imad(BITS, ebits, WINDOW, "trunc")
     achieved = imad * B / (ms_step / 1e3) / 1e12
-    peak_clock = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak_clock = float(json.load(f).get("sm_max_mhz", peak_clock))
-    except Exception:
-        pass
-    peak = sms * imad_rate * peak_clock * 1e6 / 1e12
+    peak = imad_peak(sms, imad_rate)
+    peak_clock = peak * 1e12 / (sms * imad_rate * 1e6)
     obs_clock = clocks["sm_mhz"] or imad_mhz
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
                 "traffic": traffic,
@@ -368,6 +369,37 @@ def main():
         rate, cores, count, dt = cpu_oracle_rate(b, ebits, args.cpu_budget)
         cpu = {"value": rate, "unit": "modexp/s", "cores": cores, "kind": "oracle",
                "sample": f"{count} of the 65536 instances ({dt:.1f} s), plain square-and-multiply"}
+
+    # parity of the timed configuration: every instance against the oracle, in a host thread
+    # (the oracle's native call releases the interpreter) while the GPU measures the batched
+    # and served forms; on rank 0 only, two cores left to the serving loop
+    parity = None
+    checker = None
+    if rank == 0:
+        import oracle
+        box = {}
+        full = not args.sampled_parity
+        idx = np.arange(B) if full else np.linspace(0, B - 1, 24).astype(int)
+        threads = max(1, (os.cpu_count() or 2) - 2)
+
+        def check():
+            t0 = time.perf_counter()
+            want = oracle.modexp(b.a[idx], b.e[idx], ebits, b.N[idx], threads)
+            box["mismatches"] = int((got_all[idx] != want).any(axis=1).sum())
+            box["seconds"] = time.perf_counter() - t0
+        checker = threading.Thread(target=check, daemon=True)
+        checker.start()
+
+    # the batched (mixed sizes) and served forms, with their roofline fractions
+    mixed = serving = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        mixed = run_mixed(max(2, args.steps // 4), 2, 100000, peak)
+        serving = run_serving((1e4, 1e5, 1e6), seconds=10.0, min_requests=100000, peak=peak)
+    if checker is not None:
+        checker.join()
+        parity = {"checked": int(idx.size), "mismatches": box["mismatches"],
+                  "oracle_seconds": round(box["seconds"], 1), "oracle_threads": threads,
+                  "kind": "every instance" if full else "sampled"}
 
     if rank == 0:
         line = {
@@ -394,6 +426,8 @@ def main():
                               "tkara": mm["tkara_sqr"]},
             "parity": parity,
             "imad_microbench": {"per_clk_per_sm": imad_rate, "implied_mhz": imad_mhz},
+            "mixed": mixed,
+            "serving": serving,
         }
         print(json.dumps(line))
     ctx.free()
@@ -514,12 +548,32 @@ def bench_4096(args):
     print(json.dumps(line))
 
 
-def bench_mixed(args):
-    """Mixed sizes: 100000 exponentiations, 40% 2048 / 25% 1024 / 20% 3072 / 15% 4096 bits,
-    full-length exponents. The autotuner picks shape and window per size; then three forms are
-    timed: one launch per size (plain), one persistent launch over all sizes, and that launch
-    replayed from a CUDA graph together with the host->device input copies and the result copy
-    (end to end). One JSON line; `value` is the persistent launch's modexp/s."""
+def imad_peak(sms: int, imad_rate: float) -> float:
+    """Roofline denominator in T IMAD/s: SMs x measured multiply-adds per SM per clock x the
+    maximum SM clock (MEASURED_PEAKS.json when present)."""
+    peak_clock = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak_clock = float(json.load(f).get("sm_max_mhz", peak_clock))
+    except Exception:
+        pass
+    return sms * imad_rate * peak_clock * 1e6 / 1e12
+
+
+def fixed_base_imad(bits: int, ebits: int, w: int) -> int:
+    """Multiply-adds of one fixed-base request on a resident table (truncated reduction): the
+    window loop and the product with 1, no table build and no conversion of the base."""
+    c = imad_counts((bits + 31) // 32)
+    windows = (ebits + w - 1) // w
+    return windows * w * c["sqr_trunc"] + (windows + 1) * c["mul_trunc"]
+
+
+def run_mixed(steps: int, warmup: int, total: int = 100000, peak: float | None = None, log=None):
+    """Mixed sizes: `total` exponentiations, 40% 2048 / 25% 1024 / 20% 3072 / 15% 4096 bits,
+    full-length exponents. The autotuner picks shape and window per size; three forms are
+    timed: one launch per size (plain), the mixed call over all sizes (one launch per job on
+    parallel streams, costliest first), and the mixed call replayed from a CUDA graph together
+    with the host->device input copies and the result copies (end to end)."""
     import numpy as np
     import seeded_inputs as si
     import torch
@@ -527,11 +581,9 @@ def bench_mixed(args):
     from paper_2410_18129_gb300 import tune
     import oracle
 
-    total = 100000 if args.batch == 65536 else args.batch
     sizes = si.mixed_sizes(0, total)
     classes = [(bits, int((sizes == bits).sum())) for bits in (4096, 3072, 2048, 1024)]
     batches = {bits: si.make_batch(0, "mixed", cnt, bits, sub=bits) for bits, cnt in classes}
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     timed = _event_timer(torch, stream)
     choice = tune.load_or_tune(sizes=(1024, 2048, 3072, 4096))
@@ -567,7 +619,7 @@ def bench_mixed(args):
         for (Y, *_), (hA, hE, hY) in zip(jobs, host):
             hY.copy_(Y, non_blocking=True)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain()
         mixed()
         e2e()
@@ -581,89 +633,158 @@ def bench_mixed(args):
     torch.cuda.synchronize()
     with torch.cuda.graph(graph):
         e2e()
-    k = max(2, args.steps)
+    k = max(2, steps)
     ms_plain = timed(plain, k)
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         ms_mixed = timed(mixed, k)
     ms_graph = timed(graph.replay, k)
-    # the same persistent launch with the word-serial CIOS reduction (Alg. 4), for comparison
     cios = lambda: mp.modexp_consttime_mixed(jobs, mp.RED_CIOS, ws)
     cios()
     ms_cios = timed(cios, k)
     # parity: each size class, sampled instances of the graph-replayed results vs the oracle
     torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
     mism, sampled = 0, 0
     for (bits, cnt), (hA, hE, hY) in zip(classes, host):
         b = batches[bits]
         got = mp.deinterleave(hY.numpy().view(np.uint32), cnt, b.n)
-        idx = np.linspace(0, cnt - 1, 4).astype(int)
+        idx = np.linspace(0, cnt - 1, 6).astype(int)
         want = oracle.modexp(b.a[idx], b.e[idx], b.ebits, b.N[idx])
         mism += int((got[idx] != want).any(axis=1).sum())
         sampled += idx.size
+    imad = sum(cnt * modexp_imad(bits, bits, choice[str(bits)]["window"], "trunc") for bits, cnt in classes)
     h2d = sum((hA.numel() + hE.numel()) * 4 for hA, hE, _ in host)
     d2h = sum(hY.numel() * 4 for *_, hY in host)
-    line = {
-        "metric": "mixed-size const-time modexp/s (one persistent launch; CUDA graph end to end)",
-        "value": total / (ms_mixed / 1e3), "unit": "modexp/s", "n_gpus": 1, "steps": k, "warmup": args.warmup,
-        "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": f"mixed: {total} modexp, sizes " + ", ".join(f"{c} x {b}" for b, c in classes)
-                               + " bits, random odd moduli, full-length exponents, truncated Montgomery",
-                   "tuned": {b: {k2: v for k2, v in c.items() if k2 != "timings"} for b, c in choice.items()}},
+
+    def roof(ms):
+        achieved = imad / (ms / 1e3) / 1e12
+        return {"achieved": achieved, "frac": achieved / peak if peak else None}
+
+    out = {
+        "workload": f"mixed: {total} modexp, sizes " + ", ".join(f"{c} x {b}" for b, c in classes)
+                    + " bits, random odd moduli, full-length exponents, truncated Montgomery",
+        "modexp_per_s": total / (ms_mixed / 1e3), "ms_per_step": ms_mixed, "steps": k,
+        "form": "one launch per job on parallel streams, costliest first",
         "plain_per_size_launches_per_s": total / (ms_plain / 1e3),
-        "cios_persistent_per_s": total / (ms_cios / 1e3),
+        "speedup_vs_plain": ms_plain / ms_mixed,
+        "cios_mixed_per_s": total / (ms_cios / 1e3),
         "e2e": {"value": total / (ms_graph / 1e3), "unit": "modexp/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "form": "CUDA graph: H2D copies + persistent launch + D2H copies"},
-        "gpu_launches": 1, "clocks": clk.summary(), "parity": {"sampled": sampled, "mismatches": mism},
+                "d2h_bytes_per_step": d2h, "form": "CUDA graph: H2D copies + mixed call + D2H copies"},
+        "roofline": {"bound": "alu", "unit": "TIMAD/s", "peak": peak, "imad_per_step": imad,
+                     **roof(ms_mixed), "plain": roof(ms_plain)},
+        "tuned": {b: {k2: v for k2, v in c.items() if k2 != "timings"} for b, c in choice.items()},
+        "clocks": clk.summary(), "parity": {"sampled": sampled, "mismatches": mism},
     }
-    print(json.dumps(line))
     for c in ctxs:
         c.free()
+    return out
 
 
-def bench_serving(args):
-    """Serving: Poisson arrivals at 1e4..1e6 req/s over a resident pool of 4096 moduli (mixed
-    sizes, fixed bases, tables on the device). Each rate is replayed through the continuous-
-    batching loop (4 streams, one persistent launch per batch, admission by device memory) and
-    through the plain path (one batch at a time, one launch per size). Reports p50/p99 latency
-    and throughput per rate; `value` is the continuous loop's throughput at the highest rate."""
+def bench_mixed(args):
+    """--workload mixed: the mixed-size forms on their own (one JSON line; `value` is the mixed
+    call's modexp/s)."""
+    import torch
+    import paper_2410_18129_gb300 as mp
+    torch.cuda.set_device(0)
+    rate, _ = mp.bench_imad(0, 2000)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    total = 100000 if args.batch == 65536 else args.batch
+    m = run_mixed(args.steps, args.warmup, total, imad_peak(sms, rate))
+    line = {
+        "metric": "mixed-size const-time modexp/s (mixed call; CUDA graph end to end)",
+        "value": m["modexp_per_s"], "unit": "modexp/s", "n_gpus": 1, "steps": m["steps"], "warmup": args.warmup,
+        "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic", "config": {"workload": m["workload"], "tuned": m["tuned"]},
+        "e2e": m["e2e"], "roofline": m["roofline"], "gpu_launches": 4, "clocks": m["clocks"],
+        "parity": m["parity"], "plain_per_size_launches_per_s": m["plain_per_size_launches_per_s"],
+        "cios_mixed_per_s": m["cios_mixed_per_s"],
+    }
+    print(json.dumps(line))
+
+
+def run_serving(rates=(1e4, 1e5, 1e6), seconds: float = 10.0, min_requests: int = 100000, cap: int = 400000,
+                peak: float | None = None, plain: bool = True, variable_rates=(1e4, 1e5)):
+    """Serving: Poisson arrivals over a resident pool of 4096 moduli (mixed sizes, fixed bases,
+    tables on the device). Each rate runs for `seconds` of arrivals or `min_requests` requests,
+    whichever is more (at most `cap`), through the continuous-batching loop (4 streams, one
+    mixed call per batch, admission by device memory) and, for comparison, through the plain
+    path (one batch at a time, one launch per size). Reports p50/p99 latency, throughput and
+    the achieved fraction of the IMAD roofline of the served requests. The same loop then
+    serves variable-base requests (each with its own base) at `variable_rates`."""
+    import numpy as np
     import seeded_inputs as si
     import torch
     import paper_2410_18129_gb300 as mp
     from paper_2410_18129_gb300 import serve as sv
     from paper_2410_18129_gb300 import tune
 
-    torch.cuda.set_device(0)
     choice = tune.load_or_tune(sizes=(1024, 2048, 3072, 4096))
-    rates = (1e4, 3e4, 1e5, 3e5, 1e6)
-    seconds = 4.0
-    cap = 100000 if args.batch == 65536 else args.batch
     pin = si.serving_pool(0, 4096)
     pool = sv.Pool(mp, pin.sizes, pin.moduli, pin.bases)
-    traces = {r: si.poisson_trace(0, r, int(min(r * seconds, cap)), pool.sizes) for r in rates}
-    free = torch.cuda.mem_get_info()[0]
-    out = {}
-    with ClockSampler(0) as clk:
+    # free device memory, counting what torch's allocator holds unused as free
+    free_fn = lambda: torch.cuda.mem_get_info()[0] + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+
+    def run(tr, with_plain):
+        bits = pool.sizes[tr.entry]
+        var = [b is not None for b in tr.bases] if tr.bases is not None else [False] * len(bits)
+        imad = 0
+        for bb, v in zip(bits, var):
+            bb = int(bb)
+            w = pool.classes[bb]["window"]
+            imad += modexp_imad(bb, bb, w, "trunc") if v else fixed_base_imad(bb, bb, w)
+        adm = sv.AdmissionController(free_fn=free_fn, fraction=0.5, reserve=1 << 30, refresh=0.1)
+        cont = sv.serve(tr, sv.ContinuousExecutor(pool, tr, slots=4), slots=4, max_batch=16384, admission=adm)
+        cs = cont.summary()
+        span = float(np.nanmax(cont.done_at))
+        cs["roofline"] = {"achieved": imad / span / 1e12, "frac": imad / span / 1e12 / peak if peak else None,
+                          "imad": imad}
+        entry = {"requests": len(bits), "continuous": cs}
+        if with_plain:
+            entry["plain"] = sv.serve(tr, sv.PlainExecutor(pool, tr), slots=1, max_batch=16384).summary()
+        return entry
+
+    out, out_var = {}, {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
         for r in rates:
-            tr = traces[r]
-            adm = sv.AdmissionController(free_fn=lambda: free, fraction=0.5, reserve=1 << 30)
-            cont = sv.serve(tr, sv.ContinuousExecutor(pool, tr, slots=4), slots=4, max_batch=16384, admission=adm)
-            plain = sv.serve(tr, sv.PlainExecutor(pool, tr), slots=1, max_batch=16384)
-            out[f"{r:.0e}"] = {"offered_per_s": r, "continuous": cont.summary(), "plain": plain.summary()}
-    top = out[f"{rates[-1]:.0e}"]["continuous"]
+            count = int(min(cap, max(r * seconds, min_requests)))
+            tr = si.poisson_trace(0, r, count, pool.sizes)
+            out[f"{r:.0e}"] = {"offered_per_s": r, **run(tr, plain and r < 1e6)}
+        for r in variable_rates:
+            count = int(min(cap, max(r * seconds, min_requests)))
+            tr = si.with_bases(si.poisson_trace(1, r, count, pool.sizes), pin, 1.0)
+            out_var[f"{r:.0e}"] = {"offered_per_s": r, **run(tr, False)}
+    res = {
+        "workload": "serving: pool of 4096 moduli (1639 x 2048, 1024 x 1024, 819 x 3072, 614 x 4096 bits), fixed "
+                    "base per modulus with resident tables, full-length exponents, Poisson arrivals, "
+                    f">= {seconds:.0f} s or >= {min_requests} requests per rate",
+        "windows": {b: c["window"] for b, c in choice.items()}, "slots": 4, "max_batch": 16384,
+        "rates": out, "variable_base_rates": out_var,
+        "variable_base": "every request brings its own base: its window table (2^w - 2 more products) is built "
+                         "per request", "clocks": clk.summary(),
+    }
+    pool.free()
+    return res
+
+
+def bench_serving(args):
+    """--workload serving: the serving loop on its own (one JSON line; `value` is the continuous
+    loop's throughput at the highest rate)."""
+    import torch
+    import paper_2410_18129_gb300 as mp
+    torch.cuda.set_device(0)
+    rate, _ = mp.bench_imad(0, 2000)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = run_serving((1e4, 3e4, 1e5, 3e5, 1e6), peak=imad_peak(sms, rate))
+    top = res["rates"]["1e+06"]["continuous"]
     line = {
         "metric": "serving: p50/p99 latency and throughput under Poisson load (mixed sizes, resident moduli)",
-        "value": top["throughput_per_s"], "unit": "modexp/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
+        "value": top["throughput_per_s"], "unit": "modexp/s", "n_gpus": 1, "steps": len(res["rates"]), "warmup": 0,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": "serving: pool of 4096 moduli (1639 x 2048, 1024 x 1024, 819 x 3072, 614 x 4096 "
-                               "bits), fixed base per modulus with resident tables, full-length exponents, "
-                               f"Poisson arrivals, up to {seconds:.0f} s or {cap} requests per rate",
-                   "windows": {b: c["window"] for b, c in choice.items()}, "slots": 4, "max_batch": 16384},
-        "rates": out, "clocks": clk.summary(),
+        "data": "synthetic", "config": {k: v for k, v in res.items() if k not in ("rates", "clocks")},
+        "rates": res["rates"], "clocks": res["clocks"],
     }
     print(json.dumps(line))
-    pool.free()
 
 
 if __name__ == "__main__":

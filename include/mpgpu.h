@@ -189,9 +189,12 @@ typedef struct {
     uint32_t exp_bits;      /* public exponent length */
     uint32_t window;        /* 1..6, 0 = tuned (fixed-base jobs: the tables' window) */
     const mont_ctx *ctx;
-    /* fixed-base job when index != NULL: nreq requests, request i uses context instance
-       index[i] and its resident table in `tables` (see modexp_table_build); y and exp then
-       hold nreq instances */
+    /* routed job when index != NULL: nreq requests, request i uses context instance index[i]
+       (its modulus; a resident pool of moduli); y and exp then hold nreq instances.
+       With tables != NULL the job is fixed-base: request i runs on the resident table of
+       instance index[i] (see modexp_table_build) and base is unused. With tables == NULL
+       request i brings its own base (base holds nreq instances) and its table is built in
+       the workspace like an ordinary job's. */
     const uint32_t *index;
     const void *tables;
     size_t nreq;

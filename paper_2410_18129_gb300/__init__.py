@@ -193,14 +193,16 @@ class _Job(ctypes.Structure):
 
 def _jobs(jobs):
     """jobs: sequence of (y, base, exp, exp_bits, ctx, window) for exponentiations of a
-    context's own bases, or (y, None, exp, exp_bits, ctx, window, index, tables, nreq) for
-    fixed-base requests on resident tables -> ctypes array."""
+    context's own bases, or (y, base, exp, exp_bits, ctx, window, index, tables, nreq) for
+    requests routed to context instances: fixed-base on resident tables (base None, tables
+    given) or with their own bases (tables None) -> ctypes array."""
     arr = (_Job * len(jobs))()
     for i, job in enumerate(jobs):
         y, base, exp, exp_bits, ctx, window = job[:6]
         if len(job) > 6:
             index, tables, nreq = job[6:9]
-            arr[i] = _Job(_ptr(y), None, _ptr(exp), exp_bits, window, ctx.handle, _ptr(index), _ptr(tables), nreq)
+            arr[i] = _Job(_ptr(y), _ptr(base), _ptr(exp), exp_bits, window, ctx.handle, _ptr(index), _ptr(tables),
+                          nreq)
         else:
             arr[i] = _Job(_ptr(y), _ptr(base), _ptr(exp), exp_bits, window, ctx.handle, None, None, 0)
     return arr

@@ -82,12 +82,13 @@ struct KArgs {
     const uint32_t *R1;
     const uint32_t *R2;
     const uint32_t *K;
-    uint32_t *table;         // window tables: [entry][NP/4][cbatch] uint4
+    uint32_t *table;         // window tables: [entry][NP/4][instances] uint4, one per request (mode 0)
+                             // or per context instance (modes 1, 2)
     size_t batch;            // instances of the API arrays (requests)
     int n;                   // API words per value
     int layout;              // API layout
     int ebits, ne, window, red, square, correct;
-    const uint32_t *index;   // fixed-base requests: request k uses context instance index[k]
+    const uint32_t *index;   // routed requests: request k uses context instance index[k]
     size_t cbatch;           // instances of the context arrays and tables (== batch without index)
     int mode;                // exponentiation: 0 build the table and run, 1 build only, 2 run on a resident table
     int lazy;                // exponentiation: 4N <= W^NP, products skip the final subtraction (results < 2N)
@@ -220,9 +221,8 @@ MPG_DI uint32_t window_bits(const KArgs &A, size_t k, bool valid, int pos, int w
 }
 
 // One group's constant-time exponentiation (Alg. 7) of request k. Request k uses
-// context instance kc = index[k] (fixed-base requests on a resident pool) or k.
-// Shared by the one-size kernel and the mixed-size persistent kernel.
-//   mode 0: build the window table of base k, then run the windows
+// context instance kc = index[k] (requests routed to a resident pool of moduli) or k.
+//   mode 0: build the window table of request k's base, then run the windows
 //   mode 1: only build the table (a resident table for later fixed-base requests)
 //   mode 2: run the windows on the resident table of instance kc
 template <class S, int RED>
@@ -233,7 +233,10 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     valid = valid && kc < A.cbatch;
     const int w = A.window;
     const int E = 1 << w;
-    const size_t cb = A.cbatch;
+    // window table and base: per request when the job builds its tables (mode 0, also when
+    // its requests are routed to context instances), per context instance for resident tables
+    const size_t kt = A.mode == 0 ? k : kc;
+    const size_t tb = A.mode == 0 ? A.batch : A.cbatch;
     uint4 *tab = reinterpret_cast<uint4 *>(A.table);
 
     auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
@@ -243,13 +246,13 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
         if constexpr (M % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c)
-                tab[tidx4<S>(e, g.t * (M / 4) + c, kc, cb)] =
+                tab[tidx4<S>(e, g.t * (M / 4) + c, kt, tb)] =
                     make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
         } else {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = g.t * M + j;
-                A.table[tidx4<S>(e, i >> 2, kc, cb) * 4 + (i & 3)] = x[j];
+                A.table[tidx4<S>(e, i >> 2, kt, tb) * 4 + (i & 3)] = x[j];
             }
         }
     };
@@ -258,14 +261,14 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c) {
                 uint4 v = make_uint4(0, 0, 0, 0);
-                if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, kc, cb)];
+                if (valid) v = tab[tidx4<S>(e, g.t * (M / 4) + c, kt, tb)];
                 x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = g.t * M + j;
-                x[j] = valid ? A.table[tidx4<S>(e, i >> 2, kc, cb) * 4 + (i & 3)] : 0u;
+                x[j] = valid ? A.table[tidx4<S>(e, i >> 2, kt, tb) * 4 + (i & 3)] : 0u;
             }
         }
     };
@@ -282,7 +285,7 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     const int windows = (A.ebits + w - 1) / w;
     const int nwin = A.mode != 1 ? windows * (w + 1) + 1 : 0;
     if (A.mode != 2) {
-        load_api<S>(g, g.X(), A.a, A, kc, valid);
+        load_api<S>(g, g.X(), A.a, A, kt, valid);
         load_ctx<S>(g, g.Y(), A.R2, A, kc, valid);
     } else {
         load_ctx<S>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form

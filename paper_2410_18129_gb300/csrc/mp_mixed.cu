@@ -46,13 +46,17 @@ static cudaError_t pool_init(MixPool &p) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t job_table_bytes(const mp_modexp_job &j) {
-    if (j.index) return 0;   // fixed-base job: resident tables
-    const uint32_t w = j.window ? j.window : default_window(j.ctx->bits);
-    return ((size_t)1 << w) * (size_t)j.ctx->np * j.ctx->batch * 4;
-}
+// fixed-base job: resident tables; otherwise one table per request (per context instance
+// without routing)
+static bool job_fixed(const mp_modexp_job &j) { return j.index && j.tables; }
 
 static size_t job_instances(const mp_modexp_job &j) { return j.index ? j.nreq : j.ctx->batch; }
+
+static size_t job_table_bytes(const mp_modexp_job &j) {
+    if (job_fixed(j)) return 0;
+    const uint32_t w = j.window ? j.window : default_window(j.ctx->bits);
+    return ((size_t)1 << w) * (size_t)j.ctx->np * job_instances(j) * 4;
+}
 
 }  // namespace mpg
 
@@ -64,7 +68,7 @@ static int check_jobs(const mp_modexp_job *jobs, int njobs) {
     for (int i = 0; i < njobs; ++i) {
         const mp_modexp_job &j = jobs[i];
         if (!j.y || !j.ctx || (j.exp_bits > 0 && !j.exp)) return MP_ERR_ARG;
-        if (j.index ? (!j.tables || j.nreq == 0 || j.window == 0) : !j.base) return MP_ERR_ARG;
+        if (j.index ? (j.nreq == 0 || (j.tables ? j.window == 0 : !j.base)) : !j.base) return MP_ERR_ARG;
         if (j.window > 6) return MP_ERR_SIZE;
         if (j.index && ((uintptr_t)j.tables & 15u)) return MP_ERR_ALIGN;
         if (j.ctx->layout == MP_LAYOUT_INTERLEAVED &&
@@ -116,12 +120,14 @@ extern "C" int modexp_consttime_mixed(const mp_modexp_job *jobs, int njobs, mp_r
         A.ne = j.exp_bits ? (int)((j.exp_bits + 31) / 32) : 1;
         A.window = (int)(j.window ? j.window : default_window(j.ctx->bits));
         A.red = (int)red;
-        if (j.index) {   // fixed-base requests on resident tables
+        if (j.index) {   // requests routed to context instances
             A.index = j.index;
             A.batch = j.nreq;
+        }
+        if (job_fixed(j)) {   // fixed bases: resident tables
             A.table = const_cast<uint32_t *>(reinterpret_cast<const uint32_t *>(j.tables));
             A.mode = 2;
-        } else {
+        } else {              // own bases: tables built in the workspace, one per request
             A.table = reinterpret_cast<uint32_t *>(ws + off);
             off += align256(job_table_bytes(j));
         }

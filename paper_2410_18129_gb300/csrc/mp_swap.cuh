@@ -582,7 +582,10 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
     valid = valid && kc < A.cbatch;
     const int w = A.window;
     const int E = 1 << w;
-    const size_t cb = A.cbatch;
+    // window table and base: per request when the job builds its tables (mode 0, also when
+    // its requests are routed to context instances), per context instance for resident tables
+    const size_t kt = A.mode == 0 ? k : kc;
+    const size_t tb = A.mode == 0 ? A.batch : A.cbatch;
     uint4 *tab = reinterpret_cast<uint4 *>(A.table);
 
     auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
@@ -592,12 +595,12 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
         if constexpr (M % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c)
-                tab[tidx4<PS>(e, g.t * (M / 4) + c, kc, cb)] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+                tab[tidx4<PS>(e, g.t * (M / 4) + c, kt, tb)] = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
         } else {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = g.t * M + j;
-                A.table[tidx4<PS>(e, i >> 2, kc, cb) * 4 + (i & 3)] = x[j];
+                A.table[tidx4<PS>(e, i >> 2, kt, tb) * 4 + (i & 3)] = x[j];
             }
         }
     };
@@ -606,14 +609,14 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c) {
                 uint4 q = make_uint4(0, 0, 0, 0);
-                if (valid) q = tab[tidx4<PS>(e, g.t * (M / 4) + c, kc, cb)];
+                if (valid) q = tab[tidx4<PS>(e, g.t * (M / 4) + c, kt, tb)];
                 x[4 * c] = q.x; x[4 * c + 1] = q.y; x[4 * c + 2] = q.z; x[4 * c + 3] = q.w;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = g.t * M + j;
-                x[j] = valid ? A.table[tidx4<PS>(e, i >> 2, kc, cb) * 4 + (i & 3)] : 0u;
+                x[j] = valid ? A.table[tidx4<PS>(e, i >> 2, kt, tb) * 4 + (i & 3)] : 0u;
             }
         }
     };
@@ -624,7 +627,7 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
     const int windows = (A.ebits + w - 1) / w;
     const int nwin = A.mode != 1 ? windows * (w + 1) + 1 : 0;
     if (A.mode != 2) {
-        load_api<PS>(g, g.X(), A.a, A, kc, valid);
+        load_api<PS>(g, g.X(), A.a, A, kt, valid);
         load_ctx<PS>(g, g.Y(), A.R2, A, kc, valid);
     } else {
         load_ctx<PS>(g, g.X(), A.R1, A, kc, valid);     // Y_acc = 1 in Montgomery form

@@ -281,10 +281,13 @@ def mixed_sizes(seed: int, count: int) -> np.ndarray:
 @dataclass
 class Trace:
     """A request trace: arrival times (s, increasing), the pool entry each request uses,
-    and its exponent words (full length for that entry's size, instance-major)."""
+    and its exponent words (full length for that entry's size, instance-major). bases:
+    None for a fixed-base trace, else per request its own base words (below the entry's
+    modulus) or None for a request on the entry's fixed base."""
     arrival: np.ndarray      # float64 [count]
     entry: np.ndarray        # int64 [count], index into the pool
     exponents: list          # per request: uint32 words
+    bases: list | None = None
 
 
 def pool_sizes(seed: int, count: int) -> np.ndarray:
@@ -326,3 +329,23 @@ def poisson_trace(seed: int, rate: float, count: int, sizes: np.ndarray) -> Trac
         bits = int(sizes[k])
         exps.append(random_bits(re, 1, bits)[0])
     return Trace(arrival, entry, exps)
+
+
+def with_bases(trace: Trace, pool: PoolInputs, fraction: float, seed: int = 0) -> Trace:
+    """The same trace with a fraction of its requests (chosen with the seed) carrying their own
+    base, uniform below the modulus of their pool entry."""
+    r = stream(seed, "serving", "base", int(1e6 * fraction))
+    pick = r.random(len(trace.arrival)) < fraction
+    local = {}
+    for bits in pool.moduli:
+        ids = np.nonzero(pool.sizes == bits)[0]
+        local.update({int(k): i for i, k in enumerate(ids)})
+    bases = []
+    for k, (e, v) in enumerate(zip(trace.entry, pick)):
+        if not v:
+            bases.append(None)
+            continue
+        bits = int(pool.sizes[e])
+        N = pool.moduli[bits][local[int(e)]][None, :]
+        bases.append(uniform_below(r, N, bits)[0])
+    return Trace(trace.arrival, trace.entry, trace.exponents, bases)

@@ -445,6 +445,32 @@ def test_mixed_matches_per_size(mp, layout):
             assert_equal(got[idx], want, f"mixed vs oracle {b.bits} red={red}")
 
 
+def test_mixed_routed_own_base_jobs(mp):
+    """Requests routed to the instances of a context (a pool of moduli) with their own bases:
+    each request's table is built per request; repeated and ragged entries; beside a
+    fixed-base job on resident tables of the same context."""
+    bits, pool, w = 2048, 10, 5
+    b = si.make_batch(0, "mixed", pool, bits, ebits=1, sub=40)
+    ctx = mp.MontCtx(dev(mp, b.N, IL), pool, bits, IL)
+    tables = torch.empty(mp.modexp_table_bytes(ctx, w) // 4, dtype=torch.int32, device="cuda")
+    mp.modexp_table_build(tables, dev(mp, b.a, IL), ctx, w)
+    rng = si.stream(0, "test", "other", 41)
+    for nreq in (1, 37):
+        idx = rng.integers(0, pool, size=nreq).astype(np.uint32)
+        base = si.uniform_below(rng, b.N[idx], bits)
+        e = si.random_bits(rng, nreq, 300)
+        Y1, Y2 = out_tensor(mp, nreq, b.n, IL), out_tensor(mp, nreq, b.n, IL)
+        d_idx, d_e = mp.to_device(idx), dev(mp, e, IL)
+        jobs = [(Y1, dev(mp, base, IL), d_e, 300, ctx, w, d_idx, None, nreq),
+                (Y2, None, d_e, 300, ctx, w, d_idx, tables, nreq)]
+        for red in (0, 1, 2):
+            mp.modexp_consttime_mixed(jobs, red, mp.mixed_workspace(jobs))
+            torch.cuda.synchronize()
+            assert_equal(host(mp, Y1, nreq, b.n, IL), oracle.modexp(base, e, 300, b.N[idx]), f"own bases, red={red}")
+            assert_equal(host(mp, Y2, nreq, b.n, IL), oracle.modexp(b.a[idx], e, 300, b.N[idx]), f"fixed, red={red}")
+    ctx.free()
+
+
 def test_mixed_many_jobs_and_limits(mp):
     """16 jobs (more than the call's parallel streams) in one call, twice in a row; a 17th job
     is rejected before any launch."""

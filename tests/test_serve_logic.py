@@ -125,3 +125,93 @@ def test_poisson_trace_statistics():
     counts = np.bincount(tr.entry, minlength=4096)
     assert counts.max() < 20 and (tr.entry < 4096).all()
     assert all(e.shape[0] == (int(sizes[k]) + 31) // 32 for e, k in zip(tr.exponents[:50], tr.entry[:50]))
+
+
+class PartialExecutor(FakeExecutor):
+    """Like FakeExecutor, but the requests of a batch land in two parts: the first half after
+    `base`, the rest after `base + late` (a slow size class)."""
+
+    def __init__(self, clock, base=0.01, late=0.05):
+        super().__init__(clock, base=base, per_req=0.0)
+        self.late = late
+
+    def submit(self, reqs, nbytes):
+        h = super().submit(reqs, nbytes)
+        t = self.clock()
+        half = reqs.size // 2
+        h.token = {"parts": [[reqs[:half], t + self.base, False], [reqs[half:], t + self.base + self.late, False]]}
+        return h
+
+    def completed(self, h):
+        out = []
+        for p in h.token["parts"]:
+            if not p[2] and self.clock() >= p[1]:
+                p[2] = True
+                out.append(p[0])
+        return out
+
+    def done(self, h):
+        return all(p[2] for p in h.token["parts"])
+
+
+def test_requests_complete_with_their_part_of_a_batch():
+    """A request's latency ends when its own part of the batch lands, not the whole batch."""
+    clk = FakeClock()
+    ex = PartialExecutor(clk, base=0.01, late=0.05)
+    tr = trace(2e3, 400)
+    res = serve(tr, ex, slots=2, max_batch=64, clock=clk, idle=clk.advance)
+    assert np.isfinite(res.latency).all()
+    early, late = [], []
+    for start, b in ex.batches:
+        half = b.size // 2
+        early += list(res.done_at[b[:half]] - start)
+        late += list(res.done_at[b[half:]] - start)
+    assert max(early) < 0.02 and min(late) > 0.055
+
+
+def test_queued_requests_time_out():
+    """With one slot and slow batches the queue grows; requests older than the timeout are
+    dropped before they are batched (never sent to the executor), the rest are served."""
+    clk = FakeClock()
+    ex = FakeExecutor(clk, base=0.2, per_req=0.0)
+    tr = trace(5e3, 3000)
+    res = serve(tr, ex, slots=1, max_batch=100, clock=clk, idle=clk.advance, timeout=0.1)
+    sent = np.concatenate([b for _, b in ex.batches])
+    assert res.timed_out > 0 and res.timed_out + sent.size == 3000
+    assert np.isnan(res.latency).sum() == res.timed_out
+    starts = {int(r): t for t, b in ex.batches for r in b}
+    assert all(starts[r] - tr.arrival[r] <= 0.1 + 1e-3 for r in sent)
+    s = res.summary()
+    assert s["served"] == sent.size and s["timed_out"] == res.timed_out
+
+
+def test_admission_budget_is_read_again():
+    """The budget follows the free memory read every `refresh` seconds (fake clock)."""
+    clk = FakeClock()
+    free = {"v": 10_000}
+    a = AdmissionController(free_fn=lambda: free["v"], fraction=0.5, reserve=0, refresh=1.0, clock=clk)
+    assert a.budget == 5000 and a.admit(4000)
+    free["v"] = 2_000                     # another user took memory: in flight 4000 + free 2000
+    assert not a.admit(2000)              # not re-read yet (budget 5000)
+    clk.advance(1.0)
+    assert not a.admit(1) or a.budget == 3000
+    assert a.budget == 3000 and a.reads == 2
+    a.release(4000)
+    free["v"] = 20_000
+    clk.advance(1.0)
+    assert a.admit(9000) and a.budget == 10_000
+
+
+def test_variable_base_trace():
+    pool = si.serving_pool(0, 64)
+    tr = si.poisson_trace(0, 1e4, 500, pool.sizes)
+    tv = si.with_bases(tr, pool, 0.3)
+    var = [k for k, b in enumerate(tv.bases) if b is not None]
+    assert 100 < len(var) < 200
+    for k in var[:40]:
+        bits = int(pool.sizes[tv.entry[k]])
+        ids = np.nonzero(pool.sizes == bits)[0]
+        N = pool.moduli[bits][int(np.nonzero(ids == tv.entry[k])[0][0])]
+        b = tv.bases[k]
+        assert b.shape == N.shape and int("".join(f"{w:08x}" for w in b[::-1]), 16) < \
+            int("".join(f"{w:08x}" for w in N[::-1]), 16)
