@@ -10,7 +10,7 @@
  *   - Data pointers are DEVICE pointers owned by the caller (e.g. torch tensors).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Calls are asynchronous on that stream and never synchronise it, except
- *     mont_ctx_init / mont_ctx_free (documented there).
+ *     mont_ctx_init (documented there).
  *   - Return value: MP_OK (0) or a negative mp_status. Argument errors are
  *     detected on the host before any launch; launch failures map to MP_ERR_CUDA.
  *   - Layout (mp_layout) of an array of `batch` values of w words each:
@@ -47,8 +47,7 @@ typedef enum {
     MP_ERR_ALIGN = -4,          /* pointer not 16-byte aligned */
     MP_ERR_CUDA = -5,           /* a CUDA runtime call or kernel launch failed */
     MP_ERR_NOMEM = -6,          /* device allocation failed or workspace too small */
-    MP_ERR_UNIMPLEMENTED = -7,  /* combination the library does not provide */
-    MP_ERR_TIMEOUT = -8         /* a bounded device-side wait gave up (persistent kernels) */
+    MP_ERR_UNIMPLEMENTED = -7   /* combination the library does not provide */
 } mp_status;
 
 typedef enum { MP_LAYOUT_INSTANCE_MAJOR = 0, MP_LAYOUT_INTERLEAVED = 1 } mp_layout;
@@ -101,8 +100,8 @@ int mp_sqr(uint32_t *c, const uint32_t *a, size_t batch, uint32_t bits, mp_layou
  * Build a Montgomery context for `batch` moduli N (n words each, `layout`):
  * N' = (-N)^{-1} mod R, R mod N and R^2 mod N (Sec. 4: the precomputed values of
  * Alg. 3 and the R^2 used to enter the Montgomery representation).
- * Allocates device memory (owned by the context until mont_ctx_free) and
- * synchronises `stream` to report moduli errors: if any N is even, returns
+ * Allocates device memory (stream-ordered on `stream`; owned by the context until
+ * mont_ctx_free) and synchronises `stream` to report moduli errors: if any N is even, returns
  * MP_ERR_EVEN_MODULUS, stores the smallest offending instance index in
  * *bad_index (when non-NULL) and creates no context. N is copied; the caller
  * may free it afterwards. Operands of later calls use the same `layout`.
@@ -110,7 +109,10 @@ int mp_sqr(uint32_t *c, const uint32_t *a, size_t batch, uint32_t bits, mp_layou
 int mont_ctx_init(mont_ctx **ctx, const uint32_t *N, size_t batch, uint32_t bits,
                   mp_layout layout, size_t *bad_index, void *stream);
 
-/* Free a context (synchronises the device before freeing). NULL is accepted. */
+/* Free a context. Stream-ordered: the memory is returned after all work already queued on
+   the stream given to mont_ctx_init, which must still exist; work that uses the context on
+   other streams must be complete, or ordered before that point of the context's stream,
+   when this is called. Nothing else waits. NULL is accepted. */
 int mont_ctx_free(mont_ctx *ctx);
 
 /* Context properties: batch, bits, layout. Any out pointer may be NULL. */
@@ -251,15 +253,20 @@ int mp_tune_get(uint32_t bits, int *G, int *M, uint32_t *window, uint32_t *karat
  * mont_ctx_init, done beforehand.
  *   - Limit: modexp_workspace_bytes(batch, bits, window) must not exceed
  *     MPGPU_NOALLOC_SCRATCH_BYTES (16 MiB: e.g. 2048 instances of 2048 bits at w=5,
- *     512 of 4096 bits at w=6); larger batches return MP_ERR_SIZE before any work.
- *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any stream
+ *     512 of 4096 bits at w=6; mp_noalloc_scratch_bytes() returns it); larger batches
+ *     return MP_ERR_SIZE before any work.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current, then cached for the device's context; a new context, e.g. after
+ *     cudaDeviceReset, looks it up again); make that first call before any stream
  *     capture.
  *   - All calls share the array, which keeps the last call's contents (each call
  *     writes every table entry before reading it). Calls that overlap on the GPU
  *     (concurrent streams or host threads) race on it: serialise them.
  */
 #define MPGPU_NOALLOC_SCRATCH_BYTES (16u << 20)
+/* Bytes of the static array of modexp_consttime_noalloc (MPGPU_NOALLOC_SCRATCH_BYTES of the
+   library as built). */
+size_t mp_noalloc_scratch_bytes(void);
 int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
                              const mont_ctx *ctx, uint32_t window, mp_red red, mp_algo algo, void *stream);
 
@@ -273,10 +280,24 @@ int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *
  * 3: add.cc/addc.cc chains; 4: mad.wide.u32 chains fed by their own low word (counted as 2); 5: 8x8 block
  * product from mad.wide.u32 and 64-bit carry adds; 6: two independent 8x8 chain
  * products per iteration; 7: mode 2 on 256 threads per SM; 8: 10x10 block of 26-bit
- * digits summed into 64-bit columns by mad.wide.u32 (counted as 2 per product).
+ * digits summed into 64-bit columns by mad.wide.u32 (counted as 2 per product);
+ * 9 / 10: 8x8 / 4x4 block products summed into one running split-column accumulator
+ * (768 threads per SM); 11 / 12: the same with one array per block (block product plus
+ * addition); 13 / 14: 4x4 blocks with one / two split accumulators on 256 threads per SM.
  * Synchronous; allocates a small scratch buffer.
  */
 int mp_bench_imad(int mode, int iters, double *per_clk_per_sm, double *sm_mhz, void *stream);
+
+/*
+ * Measurement helper of the constant-time test (no counterpart in the paper; it checks
+ * the constant-time claim of Alg. 7): modexp_consttime with the caller's workspace and
+ * MP_ALGO_AUTO, writing also cycles[k] = SM clock cycles (clock64) from the start to the
+ * end of instance k's exponentiation, for each of the ctx's instances (cycles: device,
+ * batch 64-bit words, 8-byte aligned). Results in y as modexp_consttime's.
+ */
+int modexp_timing_probe(unsigned long long *cycles, uint32_t *y, const uint32_t *base, const uint32_t *exp,
+                        uint32_t exp_bits, const mont_ctx *ctx, uint32_t window, mp_red red,
+                        void *workspace, size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -46,6 +46,8 @@ _SIG = {
     "modexp_consttime": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp, _sz, _vp], _i),
     "mp_bench_imad": ([_i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp], _i),
     "modexp_consttime_noalloc": ([_vp, _vp, _vp, _u32, _vp, _u32, _i, _i, _vp], _i),
+    "mp_noalloc_scratch_bytes": ([], ctypes.c_size_t),
+    "modexp_timing_probe": ([_vp, _vp, _vp, _vp, _u32, _vp, _u32, _i, _vp, _sz, _vp], _i),
     "mp_shape_candidates": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), _i], _i),
     "mp_tune_set": ([_u32, _i, _i, _u32, _u32], _i),
     "mp_tune_get": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i),
@@ -182,7 +184,7 @@ def modexp_consttime(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,
     return y
 
 
-NOALLOC_SCRATCH_BYTES = 16 << 20
+NOALLOC_SCRATCH_BYTES = int(_lib.mp_noalloc_scratch_bytes())   # the library's static array
 
 
 class _Job(ctypes.Structure):
@@ -264,6 +266,16 @@ def tune_get(bits: int):
     _check(_lib.mp_tune_get(bits, ctypes.byref(G), ctypes.byref(M), ctypes.byref(w), ctypes.byref(k)),
            "mp_tune_get")
     return {"G": G.value, "M": M.value, "window": w.value, "karatsuba_from_bits": k.value}
+
+
+def modexp_timing_probe(cycles: torch.Tensor, y, base, exp, exp_bits: int, ctx: MontCtx, window: int,
+                        red: int, workspace: torch.Tensor):
+    """modexp_consttime that also writes each instance's SM clock cycles into `cycles` (an int32
+    tensor of 2 x batch words, read through .view(torch.int64))."""
+    _check(_lib.modexp_timing_probe(_ptr(cycles), _ptr(y), _ptr(base), _ptr(exp), exp_bits, ctx.handle, window, red,
+                                    _ptr(workspace), workspace.numel() * workspace.element_size(), _stream()),
+           "modexp_timing_probe")
+    return cycles
 
 
 def modexp_consttime_noalloc(y, base, exp, exp_bits: int, ctx: MontCtx, window: int = 0,

@@ -1,5 +1,6 @@
 // C ABI of the library (include/mpgpu.h): argument checks, shape dispatch,
 // Montgomery-context construction and the layout conversion kernel.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -117,7 +118,6 @@ extern "C" const char *mp_strerror(int st) {
         case MP_ERR_CUDA: return "CUDA error";
         case MP_ERR_NOMEM: return "out of device memory or workspace too small";
         case MP_ERR_UNIMPLEMENTED: return "not implemented";
-        case MP_ERR_TIMEOUT: return "device-side wait timed out";
         default: return "unknown status";
     }
 }
@@ -151,10 +151,14 @@ __global__ void k_convert(uint32_t *dst, int dl, const uint32_t *src, int sl, si
 
 static int launch_convert(uint32_t *dst, int dl, const uint32_t *src, int sl, size_t batch, int words, cudaStream_t st) {
     size_t total = (dl == LAYOUT_IL) ? (size_t)((words + 3) / 4) * 4 * batch : (size_t)words * batch;
-    unsigned blocks = (unsigned)((total + 255) / 256);
-    if (blocks > 152u * 32u) blocks = 152u * 32u;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MP_ERR_CUDA;
+    const size_t cap = (size_t)(sms > 0 ? sms : 1) * 32u;   // grid-stride loop: 32 blocks of 256 per SM at most
+    size_t blocks = (total + 255) / 256;
+    if (blocks > cap) blocks = cap;
     if (blocks == 0) blocks = 1;
-    k_convert<<<blocks, 256, 0, st>>>(dst, dl, src, sl, batch, words);
+    k_convert<<<(unsigned)blocks, 256, 0, st>>>(dst, dl, src, sl, batch, words);
     return cuda_status(cudaGetLastError());
 }
 
@@ -312,10 +316,11 @@ extern "C" int mont_ctx_init(mont_ctx **out, const uint32_t *N, size_t batch, ui
     mont_ctx *c = new (std::nothrow) mont_ctx{};
     if (!c) return MP_ERR_NOMEM;
     c->batch = batch; c->bits = bits; c->n = n; c->np = (uint32_t)sh->NP; c->layout = layout;
+    c->stream = S(stream);
     c->api_words = api_array_words(layout, batch, n);
     const size_t internal = (size_t)c->np * batch;
     const size_t total = 5 * internal + 4 * c->api_words + 4;   // +4: the error word (8 bytes, kept aligned)
-    if (cudaMalloc(&c->mem, total * 4) != cudaSuccess) {
+    if (cudaMallocAsync(&c->mem, total * 4, S(stream)) != cudaSuccess) {
         delete c;
         cudaGetLastError();
         return MP_ERR_NOMEM;
@@ -350,7 +355,7 @@ extern "C" int mont_ctx_init(mont_ctx **out, const uint32_t *N, size_t batch, ui
         }
     } while (0);
     if (rc != MP_OK) {
-        cudaFree(c->mem);
+        cudaFreeAsync(c->mem, st);
         delete c;
         return rc;
     }
@@ -360,10 +365,11 @@ extern "C" int mont_ctx_init(mont_ctx **out, const uint32_t *N, size_t batch, ui
 
 extern "C" int mont_ctx_free(mont_ctx *c) {
     if (!c) return MP_OK;
-    cudaError_t e = cudaDeviceSynchronize();
-    cudaError_t f = cudaFree(c->mem);
+    // stream-ordered: the memory goes back after everything already queued on the context's
+    // stream; no other stream or host thread waits
+    const cudaError_t e = cudaFreeAsync(c->mem, c->stream);
     delete c;
-    return (e == cudaSuccess && f == cudaSuccess) ? MP_OK : MP_ERR_CUDA;
+    return e == cudaSuccess ? MP_OK : MP_ERR_CUDA;
 }
 
 extern "C" int mont_ctx_info(const mont_ctx *c, size_t *batch, uint32_t *bits, mp_layout *layout) {
@@ -537,6 +543,29 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     return rc;
 }
 
+// measurement helper of the constant-time test: modexp_consttime plus per-instance cycles
+extern "C" int modexp_timing_probe(unsigned long long *cycles, uint32_t *y, const uint32_t *base, const uint32_t *exp,
+                                   uint32_t exp_bits, const mont_ctx *c, uint32_t window, mp_red red, void *workspace,
+                                   size_t workspace_bytes, void *stream) {
+    if (!cycles || !y || !base || !c || !workspace || (exp_bits > 0 && !exp)) return MP_ERR_ARG;
+    if (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS) return MP_ERR_ARG;
+    const ShapeOps *sh = ops_for(c, red, MP_ALGO_AUTO);
+    if (!sh) return MP_ERR_UNIMPLEMENTED;
+    if (window == 0) window = tuned_window(c->bits);
+    if (window > 6) return MP_ERR_SIZE;
+    if (((uintptr_t)cycles & 7u) || !aligned16(workspace) ||
+        (c->layout == MP_LAYOUT_INTERLEAVED && (!aligned16(y) || !aligned16(base) || (exp && !aligned16(exp)))))
+        return MP_ERR_ALIGN;
+    if (workspace_bytes < modexp_workspace_bytes(c->batch, c->bits, window)) return MP_ERR_NOMEM;
+    KArgs A{};
+    fill_ctx_args(A, c);
+    A.out = y; A.a = base; A.e = exp; A.table = reinterpret_cast<uint32_t *>(workspace);
+    A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
+    A.red = (int)red;
+    A.cycles = cycles;
+    return cuda_status(sh->modexp(A, S(stream)));
+}
+
 // ------------------------------------------------------------------ resident tables, fixed bases
 
 extern "C" size_t modexp_table_bytes(const mont_ctx *c, uint32_t window) {
@@ -588,27 +617,66 @@ extern "C" int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint3
 static __device__ __align__(256) uint4 g_noalloc_tables[MPGPU_NOALLOC_SCRATCH_BYTES / 16];
 
 static constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::atomic<uint32_t *> g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
 
-// Device address of the array on the current device. In host code the array's
-// name only stands for the device symbol, so the address comes from
-// cudaGetSymbolAddress, taken once per device with that device current.
+// The array's device address belongs to the context that loaded the library's device code
+// into the device: after cudaDeviceReset the next primary context may place it elsewhere.
+// The cache therefore keys each device's address by the id of the context current at the
+// lookup (driver functions reached through the runtime, no link to the driver library).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+struct NoallocEntry {
+    unsigned long long ctx_id;   // 0: empty
+    uint32_t *ptr;
+};
+static NoallocEntry g_noalloc[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+// id of the context current on this thread
+static int current_ctx_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS) return MP_ERR_CUDA;
+    return MP_OK;
+}
+
+// Device address of the array on the current device. In host code the array's name only
+// stands for the device symbol, so the address comes from cudaGetSymbolAddress, taken with
+// the device current, once per device and context.
 static int noalloc_tables(uint32_t **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MP_ERR_CUDA;
-    uint32_t *ptr = g_noalloc_ptr[dev].load(std::memory_order_acquire);
-    if (!ptr) {   // two threads racing here look up and store the same address
+    if (cudaSetDevice(dev) != cudaSuccess) return MP_ERR_CUDA;   // makes the primary context current
+    unsigned long long id = 0;
+    if (current_ctx_id(&id) != MP_OK) return MP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocEntry &e = g_noalloc[dev];
+    if (e.ctx_id != id || !e.ptr) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_tables) != cudaSuccess || !p) {
             cudaGetLastError();
             return MP_ERR_CUDA;
         }
-        ptr = reinterpret_cast<uint32_t *>(p);
-        g_noalloc_ptr[dev].store(ptr, std::memory_order_release);
+        e.ptr = reinterpret_cast<uint32_t *>(p);
+        e.ctx_id = id;
     }
-    *out = ptr;
+    *out = e.ptr;
     return MP_OK;
 }
+
+extern "C" size_t mp_noalloc_scratch_bytes(void) { return (size_t)MPGPU_NOALLOC_SCRATCH_BYTES; }
 
 extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const uint32_t *exp, uint32_t exp_bits,
                                         const mont_ctx *c, uint32_t window, mp_red red, mp_algo algo,

@@ -10,6 +10,7 @@ struct mont_ctx {
     size_t batch;
     uint32_t bits, n, np;
     mp_layout layout;
+    cudaStream_t stream;                           // stream of mont_ctx_init: allocation and free
     uint32_t *mem;                                 // one allocation for everything below
     uint32_t *N, *NI, *R1, *R2, *K;                // internal: interleaved, np words
     uint32_t *NI_api, *R1_api, *R2_api, *N_api;    // API layout, n words

@@ -92,6 +92,7 @@ struct KArgs {
     size_t cbatch;           // instances of the context arrays and tables (== batch without index)
     int mode;                // exponentiation: 0 build the table and run, 1 build only, 2 run on a resident table
     int lazy;                // exponentiation: 4N <= W^NP, products skip the final subtraction (results < 2N)
+    unsigned long long *cycles;   // measurement only: per request, SM clock cycles of its exponentiation
 };
 
 // instance of this thread within its block, and its thread index within the instance
@@ -349,7 +350,9 @@ __global__ void __launch_bounds__(TPB, (blocks_per_sm<S, TPB>())) k_modexp(KArgs
     extern __shared__ uint4 smem4[];
     Grp<S> g = make_group<S>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = global_instance<S, TPB>();
+    const long long t0 = clock64();
     modexp_group<S, RED>(g, A, k);
+    if (A.cycles && g.t == 0 && k < A.batch) A.cycles[k] = (unsigned long long)(clock64() - t0);
 }
 
 // ------------------------------------------------------------------ per-shape launch table

@@ -702,7 +702,10 @@ template <class W, int RED>
 __global__ void __launch_bounds__(W::TPB, (swap_blocks_per_sm<W>())) k_modexp_swap(KArgs A) {
     extern __shared__ uint4 smem4[];
     const Views<W> v = swap_views<W>(reinterpret_cast<uint32_t *>(smem4));
-    modexp_swap<W, RED>(v, A, swap_instance());
+    const size_t k = swap_instance();
+    const long long t0 = clock64();
+    modexp_swap<W, RED>(v, A, k);
+    if (A.cycles && v.p.t == 0 && k < A.batch) A.cycles[k] = (unsigned long long)(clock64() - t0);
 }
 
 // launchers: red 0 truncated, 1 classical; the word-serial reduction (red 2) passes a word

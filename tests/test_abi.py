@@ -69,3 +69,12 @@ def test_argument_errors_are_host_side(lib_path):
     h = vp()
     assert lib.mont_ctx_init(ctypes.byref(h), fake, 4, 1, 0, None, None) == -2
     assert lib.mont_ctx_init(None, fake, 4, 1024, 0, None, None) == -1
+
+
+def test_noalloc_scratch_size_matches_the_header(lib_path):
+    """The static array's size as built equals the header's constant and the binding's."""
+    lib = ctypes.CDLL(lib_path)
+    lib.mp_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    m = re.search(r"#define\s+MPGPU_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", open(HEADER).read())
+    assert m, "header constant not found"
+    assert lib.mp_noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))

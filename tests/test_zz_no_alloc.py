@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 IL = 1
 
 
-def _run_pair(mp, bits, batch, window, sub):
+def _run_pair(mp, bits, batch, window, sub, red=0, algo=0):
     b = si.make_batch(0, "test", batch, bits, sub=sub)
     dev = lambda x: mp.to_device(mp.interleave(x))
     ctx = mp.MontCtx(dev(b.N), batch, bits, IL)
@@ -21,8 +21,8 @@ def _run_pair(mp, bits, batch, window, sub):
     ws = torch.empty(mp.modexp_workspace_bytes(batch, bits, window) // 4, dtype=torch.int32, device="cuda")
     y_ref = torch.zeros_like(A)
     y_new = torch.full_like(A, -1)
-    mp.modexp_consttime(y_ref, A, E, b.ebits, ctx, window, workspace=ws)
-    mp.modexp_consttime_noalloc(y_new, A, E, b.ebits, ctx, window)
+    mp.modexp_consttime(y_ref, A, E, b.ebits, ctx, window, red, algo, workspace=ws)
+    mp.modexp_consttime_noalloc(y_new, A, E, b.ebits, ctx, window, red, algo)
     torch.cuda.synchronize()
     got = mp.deinterleave(mp.to_host(y_new), batch, b.n)
     want = mp.deinterleave(mp.to_host(y_ref), batch, b.n)
@@ -30,12 +30,18 @@ def _run_pair(mp, bits, batch, window, sub):
     return got, want
 
 
-def test_noalloc_matches_workspace_version_on_two_calls():
+# (reduction, product form): the truncated schoolbook kernels, the word-serial reduction
+# (lane-mapped kernels) and the truncated Karatsuba form (its own kernels)
+FORMS = [(0, 0), (2, 0), (0, 2)]
+
+
+@pytest.mark.parametrize("red,algo", FORMS)
+def test_noalloc_matches_workspace_version_on_two_calls(red, algo):
     import paper_2410_18129_gb300 as mp
     # first call: 2048-bit, w=5; second call: different size, batch and window, so a
     # second call that reused stale table contents would show up as a mismatch
     for bits, batch, window, sub in ((2048, 300, 5, 901), (1024, 700, 4, 902)):
-        got, want = _run_pair(mp, bits, batch, window, sub)
+        got, want = _run_pair(mp, bits, batch, window, sub, red, algo)
         bad = np.nonzero((got != want).any(axis=1))[0]
         assert bad.size == 0, f"{bits}-bit: {bad.size} instances differ, first {bad[:8]}"
 
