@@ -233,7 +233,8 @@ def modexp_mixed_workspace_bytes(jobs) -> int:
 
 
 def modexp_consttime_mixed(jobs, red: int = RED_TRUNCATED, workspace: torch.Tensor | None = None):
-    """One persistent launch over several (y, base, exp, exp_bits, ctx, window) jobs."""
+    """One call over several jobs of any sizes (see _jobs): each job runs its size class's kernel,
+    the jobs forked onto parallel streams costliest first and joined back to the current stream."""
     arr = _jobs(jobs)
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_lib.modexp_consttime_mixed(arr, len(jobs), red, _ptr(workspace), ws_bytes, _stream()),
