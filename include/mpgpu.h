@@ -239,6 +239,22 @@ int modexp_fixed_base(uint32_t *y, const uint32_t *index, const uint32_t *exp, u
 int mp_shape_candidates(uint32_t bits, int *G, int *M, int max);
 int mp_tune_set(uint32_t bits, int G, int M, uint32_t window, uint32_t karatsuba_from_bits);
 int mp_tune_get(uint32_t bits, int *G, int *M, uint32_t *window, uint32_t *karatsuba_from_bits);
+/*
+ * Montgomery products and exponentiations of the truncated reduction with MP_ALGO_AUTO use the
+ * truncated Karatsuba form (Sec. 5.1, as MP_ALGO_KARATSUBA) from `karatsuba_from_bits` bits in
+ * the class of `bits` (0: never, the built-in rule; sizes without the form keep schoolbook).
+ */
+int mp_tune_set_mont_karatsuba(uint32_t bits, uint32_t karatsuba_from_bits);
+int mp_tune_get_mont_karatsuba(uint32_t bits, uint32_t *karatsuba_from_bits);
+/*
+ * Instances of the exponentiation kernel that fit on one SM at once (the occupancy of the
+ * kernel that modexp_consttime runs for shape (G, M) of the class of `bits` with reduction
+ * `red`; MP_ALGO_KARATSUBA: the truncated Karatsuba form's kernel, G and M ignored), on the
+ * current device. A batch that is a multiple of this times the SM count runs in whole rounds.
+ * MP_ERR_ARG for a shape the class does not have, MP_ERR_UNIMPLEMENTED for a combination
+ * without a kernel.
+ */
+int mp_shape_residency(uint32_t bits, int G, int M, mp_red red, mp_algo algo, int *instances_per_sm);
 
 /*
  * modexp_consttime without any device allocation. The paper has no counterpart:

@@ -51,6 +51,9 @@ _SIG = {
     "mp_shape_candidates": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), _i], _i),
     "mp_tune_set": ([_u32, _i, _i, _u32, _u32], _i),
     "mp_tune_get": ([_u32, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_u32), ctypes.POINTER(_u32)], _i),
+    "mp_tune_set_mont_karatsuba": ([_u32, _u32], _i),
+    "mp_tune_get_mont_karatsuba": ([_u32, ctypes.POINTER(_u32)], _i),
+    "mp_shape_residency": ([_u32, _i, _i, _i, _i, ctypes.POINTER(_i)], _i),
     "modexp_mixed_workspace_bytes": ([_vp, _i], _sz),
     "modexp_consttime_mixed": ([_vp, _i, _i, _vp, _sz, _vp], _i),
     "modexp_table_bytes": ([_vp, _u32], _sz),
@@ -267,6 +270,23 @@ def tune_get(bits: int):
     _check(_lib.mp_tune_get(bits, ctypes.byref(G), ctypes.byref(M), ctypes.byref(w), ctypes.byref(k)),
            "mp_tune_get")
     return {"G": G.value, "M": M.value, "window": w.value, "karatsuba_from_bits": k.value}
+
+
+def tune_set_mont_karatsuba(bits: int, karatsuba_from_bits: int):
+    _check(_lib.mp_tune_set_mont_karatsuba(bits, karatsuba_from_bits), "mp_tune_set_mont_karatsuba")
+
+
+def tune_get_mont_karatsuba(bits: int) -> int:
+    k = ctypes.c_uint32()
+    _check(_lib.mp_tune_get_mont_karatsuba(bits, ctypes.byref(k)), "mp_tune_get_mont_karatsuba")
+    return k.value
+
+
+def shape_residency(bits: int, G: int = 0, M: int = 0, red: int = RED_TRUNCATED, algo: int = ALGO_AUTO) -> int:
+    """Instances of the exponentiation kernel resident on one SM (see mp_shape_residency)."""
+    r = ctypes.c_int()
+    _check(_lib.mp_shape_residency(bits, G, M, red, algo, ctypes.byref(r)), "mp_shape_residency")
+    return r.value
 
 
 def modexp_timing_probe(cycles: torch.Tensor, y, base, exp, exp_bits: int, ctx: MontCtx, window: int,

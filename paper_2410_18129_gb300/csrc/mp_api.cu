@@ -54,6 +54,8 @@ struct SizeClass {
     uint32_t kara_from;  // AUTO products use Karatsuba from this many bits (0: built-in rule)
     cudaError_t (*kara2)(const KArgs &, cudaStream_t);   // two-level Karatsuba products, or null
     ShapeOps tk;         // Montgomery products in the truncated Karatsuba form (mont/modexp null if absent)
+    uint32_t mont_kara_from;   // AUTO Montgomery products and exponentiations of the truncated reduction use
+                               // the Karatsuba form from this many bits (0: never)
 };
 static SizeClass g_classes[7];
 static std::once_flag g_classes_once;
@@ -408,11 +410,10 @@ void mpg::ctx_args(KArgs &A, const mont_ctx *c) { fill_ctx_args(A, c); }
 // classes from 512 to 4096 bits; AUTO and SCHOOLBOOK the schoolbook shapes; null otherwise
 static const ShapeOps *ops_for(const mont_ctx *c, mp_red red, mp_algo algo) {
     if (algo == MP_ALGO_KARATSUBA2) return nullptr;
-    if (algo == MP_ALGO_KARATSUBA) {
-        const SizeClass *cls = class_for(c->np);
-        if (red != MP_RED_TRUNCATED || !cls || !cls->tk.mont || (uint32_t)cls->tk.NP != c->np) return nullptr;
-        return &cls->tk;
-    }
+    const SizeClass *cls = class_for(c->np);
+    const bool tk_ok = red == MP_RED_TRUNCATED && cls && cls->tk.mont && (uint32_t)cls->tk.NP == c->np;
+    if (algo == MP_ALGO_KARATSUBA) return tk_ok ? &cls->tk : nullptr;
+    if (algo == MP_ALGO_AUTO && tk_ok && cls->mont_kara_from && c->bits >= cls->mont_kara_from) return &cls->tk;
     return shape_for_red(c->np, (int)red);
 }
 
@@ -491,6 +492,39 @@ extern "C" int mp_tune_get(uint32_t bits, int *G, int *M, uint32_t *window, uint
     if (M) *M = c->shapes[c->chosen].M;
     if (window) *window = tuned_window(bits);
     if (karatsuba_from_bits) *karatsuba_from_bits = c->kara_from ? c->kara_from : KARATSUBA_FROM_BITS;
+    return MP_OK;
+}
+
+extern "C" int mp_tune_set_mont_karatsuba(uint32_t bits, uint32_t karatsuba_from_bits) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    class_for(words_for(bits))->mont_kara_from = karatsuba_from_bits;
+    return MP_OK;
+}
+
+extern "C" int mp_tune_get_mont_karatsuba(uint32_t bits, uint32_t *karatsuba_from_bits) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (!karatsuba_from_bits) return MP_ERR_ARG;
+    *karatsuba_from_bits = class_for(words_for(bits))->mont_kara_from;
+    return MP_OK;
+}
+
+extern "C" int mp_shape_residency(uint32_t bits, int G, int M, mp_red red, mp_algo algo, int *instances_per_sm) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (!instances_per_sm || (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS)) return MP_ERR_ARG;
+    const SizeClass *c = class_for(words_for(bits));
+    const ShapeOps *sh = nullptr;
+    if (algo == MP_ALGO_KARATSUBA) {
+        if (red != MP_RED_TRUNCATED || !c->tk.modexp) return MP_ERR_UNIMPLEMENTED;
+        sh = &c->tk;
+    } else {
+        for (int i = 0; i < c->nshapes; ++i)
+            if (c->shapes[i].G == G && c->shapes[i].M == M) sh = &c->shapes[i];
+        if (!sh) return MP_ERR_ARG;
+    }
+    if (!sh->residency) return MP_ERR_UNIMPLEMENTED;
+    const int r = sh->residency((int)red);
+    if (r < 0) return red == MP_RED_CIOS ? MP_ERR_UNIMPLEMENTED : MP_ERR_CUDA;
+    *instances_per_sm = r;
     return MP_OK;
 }
 

@@ -364,7 +364,18 @@ struct ShapeOps {
     cudaError_t (*mont)(const KArgs &, cudaStream_t);
     cudaError_t (*modexp)(const KArgs &, cudaStream_t);
     cudaError_t (*kara)(const KArgs &, cudaStream_t);   // one-level Karatsuba product, or null
+    int (*residency)(int red);   // instances per SM of the exponentiation kernel for reduction red (< 0: error)
 };
+
+// resident instances per SM of a kernel with tpb threads, smem bytes of dynamic shared memory and
+// per_block instances per block, on the current device
+template <class F>
+static int resident_instances(F kern, int tpb, size_t smem, int per_block) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, tpb, smem) != cudaSuccess) return -1;
+    return blocks * per_block;
+}
 
 // Allow `smem` bytes of dynamic shared memory for kern on the current device, once per kernel
 // and device (function attributes belong to a device's context, so a process that drives several
@@ -414,10 +425,21 @@ struct ShapeImpl {
         }
         return A.red ? launch_k<S, TPB, 4>(k_modexp<S, TPB, 1>, A, st) : launch_k<S, TPB, 2>(k_modexp<S, TPB, 0>, A, st);
     }
+    static int residency(int red) {
+        constexpr size_t smem = (size_t)(TPB / S::G) * S::WORDS * 4;
+        constexpr int per = TPB / S::G;
+        if constexpr (S::WMAP) {
+            if (red == 2) return -1;
+        } else {
+            if (red == 2) return resident_instances(k_modexp<S, TPB, 2>, TPB, smem, per);
+        }
+        return red ? resident_instances(k_modexp<S, TPB, 1>, TPB, smem, per)
+                   : resident_instances(k_modexp<S, TPB, 0>, TPB, smem, per);
+    }
     static ShapeOps ops() {
         // the warp-mapped variant of a shape reports G < 0 (see mp_shape_candidates)
         return ShapeOps{S::WMAP ? -S::G : S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont,
-                        &modexp, nullptr};
+                        &modexp, nullptr, &residency};
     }
 };
 

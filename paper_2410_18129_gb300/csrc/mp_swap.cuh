@@ -730,6 +730,11 @@ struct SwapImpl {
         if (A.red == 2) return Lane::modexp(A, st);
         return A.red ? launch_swap<W, 3>(k_modexp_swap<W, 1>, A, st) : launch_swap<W, 2>(k_modexp_swap<W, 0>, A, st);
     }
+    static int residency(int red) {
+        if (red == 2) return Lane::residency(2);
+        return red ? resident_instances(k_modexp_swap<W, 1>, W::TPB, W::SMEM, 32)
+                   : resident_instances(k_modexp_swap<W, 0>, W::TPB, W::SMEM, 32);
+    }
 };
 
 }  // namespace mpg
@@ -742,6 +747,7 @@ struct SwapImpl {
         ShapeOps o = Lane::ops();                                                            \
         o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
         o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
+        o.residency = &SwapImpl<Swap<G, M>, Lane>::residency;                                \
         return o;                                                                            \
     }                                                                                        \
     }
@@ -754,6 +760,7 @@ struct SwapImpl {
         o.kara = &launch_kara<Shape<G, M>, Shape<G, MH>, TPBK>;                              \
         o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
         o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
+        o.residency = &SwapImpl<Swap<G, M>, Lane>::residency;                                \
         return o;                                                                            \
     }                                                                                        \
     }

@@ -252,9 +252,13 @@ struct TKaraImpl {
     static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
         return launch_k<KS, TPB, 8>(k_modexp<KS, TPB, 3>, A, st);
     }
+    static int residency(int red) {
+        if (red != 0) return -1;
+        return resident_instances(k_modexp<KS, TPB, 3>, TPB, (size_t)(TPB / KS::G) * KS::WORDS * 4, TPB / KS::G);
+    }
     static ShapeOps ops() {
         return ShapeOps{KS::G, KS::M, KS::NP, TPB, (size_t)(TPB / KS::G) * KS::WORDS * 4, nullptr, &mont, &modexp,
-                        nullptr};
+                        nullptr, &residency};
     }
 };
 
