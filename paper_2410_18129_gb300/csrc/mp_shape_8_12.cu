@@ -1,4 +1,11 @@
-// Kernels for groups of 8 threads x 12 words per thread (96 words, 3072 bits), 128 threads per block.
+// Kernels for groups of 8 threads x 12 words per thread (96 words, 3072 bits), 128 threads per
+// block; the truncated and classical Montgomery kernels role-swapped in 256-thread blocks of 32
+// instances (two per SM: 128 registers per thread for the 12-word blocks' accumulators).
 #include "mp_kara.cuh"
+#include "mp_swap.cuh"
+#ifdef MPG_LANE_ONLY
 MPG_DEFINE_SHAPE_KARA(8, 12, 128, 6, 128)
-// Karatsuba: three half products on groups of 8 threads x 6 words, 128 threads per block.
+#else
+MPG_DEFINE_SHAPE_KARA_SWAP(8, 12, 128, 6, 128)
+#endif
+// Karatsuba: three half products on groups of 8 threads x 6 words.
