@@ -37,9 +37,11 @@ using namespace mpg;
 static constexpr uint32_t MAX_NP = 144;   // largest padded size: 8 threads x 18 words
 static constexpr uint32_t MAX_BITS = 32 * MAX_NP;
 // MP_ALGO_AUTO switch-over for products: measured on GB300, schoolbook wins at every size
-// (M products/s, schoolbook vs one Karatsuba level: 4096 bits mul 263 / 205, sqr 397 / 224;
-// 4108 bits 221 / 218, 348 / 285; 4154 bits 239 / 220, 355 / 288), so AUTO never picks Karatsuba
-// unless mp_tune_set sets a switch-over
+// (M products/s at a batch of 65536, schoolbook vs one Karatsuba level; role-swapped kernels:
+// 1024 bits mul 3826 / 3035, sqr 4980 / 3454; 2048 bits 1429 / 1218, 1932 / 1504; 3072 bits
+// 762 / 661, 1175 / 907; 4096 bits 470 / 464, 671 / 662; lane-mapped: 4108 bits 221 / 218,
+// 348 / 285; 4154 bits 239 / 220, 355 / 288), so AUTO never picks Karatsuba unless mp_tune_set
+// sets a switch-over
 static constexpr uint32_t KARATSUBA_FROM_BITS = 0xffffffffu;
 
 // Size classes: one per padded size NP. Each class has one or more compiled group

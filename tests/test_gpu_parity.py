@@ -312,6 +312,33 @@ def test_karatsuba_mul_sqr(mp, bits, layout):
     assert_equal(host(mp, C, batch, 2 * n, layout), oracle.sqr(a_np), f"karatsuba sqr {bits}")
 
 
+@pytest.mark.parametrize("shape", [(16, 8), (8, 16)])
+def test_products_each_4096_bit_shape(mp, shape):
+    """Schoolbook and one-level Karatsuba products on each compiled shape of the 4096-bit class
+    (role-swapped: 16 roles x 8 words with half products of 16 x 4, and 8 x 16 with halves of
+    8 x 8), against the oracle; all-ones operands make both half sums carry out."""
+    bits, batch = 4096, 70
+    a_np = si.random_bits(si.stream(0, "test", "other", 7100), batch, bits)
+    b_np = si.random_bits(si.stream(0, "test", "other", 7101), batch, bits)
+    a_np[0] = b_np[0] = 0xFFFFFFFF
+    a_np[1] = 0
+    a_np[2, :64] = 0xFFFFFFFF                    # only the low half all ones
+    b_np[3, 64:] = 0xFFFFFFFF                    # only the high half all ones
+    saved = mp.tune_get(bits)
+    try:
+        mp.tune_set(bits, *shape)
+        for layout in (IM, IL):
+            A, B = dev(mp, a_np, layout), dev(mp, b_np, layout)
+            C = out_tensor(mp, batch, 256, layout)
+            for algo in (mp.ALGO_SCHOOLBOOK, mp.ALGO_KARATSUBA):
+                mp.mp_mul(C, A, B, batch, bits, layout, algo)
+                assert_equal(host(mp, C, batch, 256, layout), oracle.mul(a_np, b_np), f"mul {shape} {algo}")
+                mp.mp_sqr(C, A, batch, bits, layout, algo)
+                assert_equal(host(mp, C, batch, 256, layout), oracle.sqr(a_np), f"sqr {shape} {algo}")
+    finally:
+        mp.tune_set(bits, saved["G"], saved["M"], saved["window"], saved["karatsuba_from_bits"])
+
+
 def test_karatsuba_auto_and_small_sizes(mp):
     bits, batch = 4096, 9
     x = si.random_bits(si.stream(0, "test", "other", 77), batch, bits)
