@@ -28,6 +28,7 @@ namespace mpg {
 template <bool P = true>
 MPG_DI int pad32(int i) { return P ? i + ((i >> 5) << 2) : i; }
 constexpr int pad_size(int n, bool p = true) { return !p ? n : n ? (n - 1) + (((n - 1) >> 5) << 2) + 1 : 0; }
+constexpr int pad_index(int i, bool p = true) { return p ? i + ((i >> 5) << 2) : i; }
 
 template <bool P>
 struct PadMap {
@@ -50,7 +51,13 @@ struct Swap {
     static constexpr int OFF_T = LS::OFF_T;
     static constexpr int OFF_P = (OFF_T + pad_size(2 * NP, PAD) + 3) & ~3;
     static constexpr int SPILL_TOP = (pad_size(2 * G * M, PAD) + 3) & ~3;
-    static constexpr int WORDS_RAW = OFF_P + SPILL_TOP + 2 * G;
+    // one word: ((-T) mod R)[NP-1] for the carry recovery of the truncated high half (Thm. 1/2)
+    static constexpr int OFF_L = OFF_P + SPILL_TOP + 2 * G;
+    static constexpr int WORDS_RAW = OFF_L + 1;
+    // Thm. 2 boundary sums exchanged through T's low half (dead once q is formed): ZW words per
+    // thread at padded offsets, 16-byte aligned
+    static constexpr int ZW = (H + 3 + 3) & ~3;
+    static_assert(pad_index((G - 1) * ZW, PAD) + ZW <= pad_index(NP, PAD), "Z exchange must stay below T's high half");
     // product view: the 32 lanes of a warp read the same offset of 32 records; a stride of
     // 4 (mod 8) words puts each group of 8 lanes' 16-byte accesses on distinct banks
     static constexpr int WORDS = ((WORDS_RAW + 3) / 8) * 8 + 4;
@@ -84,10 +91,33 @@ MPG_DI size_t swap_instance() { return (size_t)blockIdx.x * 32 + (threadIdx.x & 
 
 MPG_DI void bsync() { __syncthreads(); }
 
-// spill words of slot s for B-word slots: hi words padded, the top word after them
+// Spill of slot s for B-word slots: its hi words B .. 2B-1 at P + pad32(s*B); its top word 2B
+// beside the top of the other slot of the same thread of the product view, so that the two go
+// out in one 8-byte store: entry top_index(s) of the 2G words at P + SPILL_TOP.
 template <class W, int B, class S>
-MPG_DI Spill swp_spill(const Grp<S> &g, int s) {
-    return Spill{g.P() + pad32<W::PAD>(s * B), g.P() + W::SPILL_TOP + s};
+MPG_DI uint32_t *swp_hi(const Grp<S> &g, int s) { return g.P() + pad32<W::PAD>(s * B); }
+
+template <int G, int PAT>
+MPG_DI int top_index(int s) {
+    if constexpr (PAT == PAT_SEQ) return 2 * (s % G) + s / G;     // thread s mod G: slots t, G+t
+    else return s < G ? 2 * s : 2 * (2 * G - 1 - s) + 1;          // zigzag: slots t, 2G-1-t
+}
+
+// store the low and hi words of a slot sum; returns its top word (word 2B; word 2B+1 is zero)
+template <int B>
+MPG_DI uint32_t store_lohi(const uint32_t (&V)[2 * B + 2], uint32_t *out_lo, uint32_t *out_hi) {
+    uint32_t lo[B], hi[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) { lo[j] = V[j]; hi[j] = V[B + j]; }
+    sts<B>(out_lo, lo);
+    sts<B>(out_hi, hi);
+    return V[2 * B];
+}
+
+// the top words of this thread's first and second slot
+template <class W, class S>
+MPG_DI void store_tops(const Grp<S> &g, uint32_t top0, uint32_t top1) {
+    *reinterpret_cast<uint2 *>(g.P() + W::SPILL_TOP + 2 * g.t) = make_uint2(top0, top1);
 }
 
 // ------------------------------------------------------------------ product-view phases
@@ -101,11 +131,16 @@ MPG_DI void swp_mul_slots(const Grp<typename W::PS> &g, const uint32_t *X, const
     constexpr int G = W::G, M = W::M, U = run_group<M>();
     const int t = g.t;
     Acc3<M> a;
+    uint32_t V[2 * M + 2];
     acc3_zero<M>(a);
     mac_run<M, U>(a, X, Y, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; });
-    flush<M>(a, T + pad32<W::PAD>(t * M), swp_spill<W, M>(g, t));
+    acc3_value<M>(V, a);
+    const uint32_t top0 = store_lohi<M>(V, T + pad32<W::PAD>(t * M), swp_hi<W, M>(g, t));
+    acc3_zero<M>(a);
     mac_run<M, U>(a, X, Y, G - 1 - t, [&](int j, int &u, int &v) { u = t + 1 + j; v = G - 1 - j; });
-    park<M>(a, T + pad32<W::PAD>((G + t) * M), swp_spill<W, M>(g, G + t));
+    acc3_value<M>(V, a);
+    const uint32_t top1 = store_lohi<M>(V, T + pad32<W::PAD>((G + t) * M), swp_hi<W, M>(g, G + t));
+    store_tops<W>(g, top0, top1);
 }
 
 // V (2M+2 words, below W^(2M+1) / 2) <- 2 V + the squares x_i^2 at columns 2i
@@ -139,6 +174,7 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
     const int nA = (t + 1) >> 1;              // pairs u < v with u + v = t
     const int nB = ((G - t + 1) >> 1) - 1;    // pairs with u + v = G + t
     Acc3<M> a;
+    uint32_t top[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int s = k ? G + t : t;
@@ -155,8 +191,9 @@ MPG_DI void swp_sqr_slots(const Grp<typename W::PS> &g, const uint32_t *X, uint3
         uint32_t V[2 * M + 2];
         acc3_value<M>(V, a);
         double_add_diag<M>(V, x);
-        store_slot<M>(V, T + pad32<W::PAD>(s * M), swp_spill<W, M>(g, s));
+        top[k] = store_lohi<M>(V, T + pad32<W::PAD>(s * M), swp_hi<W, M>(g, s));
     }
+    store_tops<W>(g, top[0], top[1]);
 }
 
 // slot sums of q = T_lo * N' mod R in H-word slots: thread t owns slots t (t+1 blocks) and
@@ -166,11 +203,16 @@ MPG_DI void swp_mullo_slots(const Grp<typename W::PS> &g, const uint32_t *T, con
     constexpr int G = W::G, H = W::H, U = run_group<H>();
     const int t = g.t;
     Acc3<H> a;
+    uint32_t V[2 * H + 2];
     acc3_zero<H>(a);
     mac_run<H, U>(a, T, NI, t + 1, [&](int j, int &u, int &v) { u = j; v = t - j; }, PadMap<W::PAD>{});
-    flush<H>(a, Q + t * H, swp_spill<W, H>(g, t));
+    acc3_value<H>(V, a);
+    const uint32_t top0 = store_lohi<H>(V, Q + t * H, swp_hi<W, H>(g, t));
+    acc3_zero<H>(a);
     mac_run<H, U>(a, T, NI, 2 * G - t, [&](int j, int &u, int &v) { u = j; v = 2 * G - 1 - t - j; }, PadMap<W::PAD>{});
-    park<H>(a, Q + (2 * G - 1 - t) * H, swp_spill<W, H>(g, 2 * G - 1 - t));
+    acc3_value<H>(V, a);
+    const uint32_t top1 = store_lohi<H>(V, Q + (2 * G - 1 - t) * H, swp_hi<W, H>(g, 2 * G - 1 - t));
+    store_tops<W>(g, top0, top1);
 }
 
 // slot sums of the classical reduction T + q*N over all 2*NP words: T's words of a slot are
@@ -180,6 +222,7 @@ MPG_DI void swp_fma_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, cons
     constexpr int G = W::G, M = W::M, U = run_group<M>();
     const int t = g.t;
     Acc3<M> a;
+    uint32_t top[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int s = k ? G + t : t;
@@ -195,8 +238,9 @@ MPG_DI void swp_fma_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, cons
 #pragma unroll
         for (int j = M; j < 2 * M + 1; ++j) addc_cc(V[j], 0u);
         addc(V[2 * M + 1], 0u);
-        store_slot<M>(V, T + pad32<W::PAD>(s * M), swp_spill<W, M>(g, s));
+        top[k] = store_lohi<M>(V, T + pad32<W::PAD>(s * M), swp_hi<W, M>(g, s));
     }
+    store_tops<W>(g, top[0], top[1]);
 }
 
 // Boundary terms of Thm. 2 for one H x H block product X*Y on the diagonal u + v = 2G-1, whose
@@ -286,15 +330,15 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
             mad_hi_cc(z.h0, xq, yn);
             addc(z.h1, 0u);
         }
-        uint32_t Z[H + 3];
+        uint32_t Z[H + 3], Zs[W::ZW];
         zacc_value<H>(Z, z);
-        static_assert(G * (H + 3) <= NP - 1, "Z exchange must stay below word NP-1 of T");
-        uint32_t *zs = g.T() + t * (H + 3);
 #pragma unroll
-        for (int k = 0; k < H + 3; ++k) zs[k] = Z[k];
+        for (int k = 0; k < W::ZW; ++k) Zs[k] = k < H + 3 ? Z[k] : 0u;
+        sts<W::ZW>(g.T() + pad32<W::PAD>(t * W::ZW), Zs);
     }
     constexpr int U = run_group<H>();
     Acc3<H> a;
+    uint32_t top[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int s = k ? 2 * G - 1 - t : t;
@@ -310,8 +354,9 @@ MPG_DI void swp_mulhi_slots(const Grp<typename W::PS> &g, const uint32_t *Qs, co
 #pragma unroll
         for (int j = H; j < 2 * H + 1; ++j) addc_cc(V[j], 0u);
         addc(V[2 * H + 1], 0u);
-        store_slot<H>(V, C + s * H, swp_spill<W, H>(g, s));
+        top[k] = store_lohi<H>(V, C + s * H, swp_hi<W, H>(g, s));
     }
+    store_tops<W>(g, top[0], top[1]);
 }
 
 // ------------------------------------------------------------------ carry-view phases
@@ -343,7 +388,7 @@ MPG_DI uint32_t cv_resolve(const Grp<typename W::LS> &g, const uint32_t (&in0)[B
             lds<B>(h, g.P() + pad32<W::PAD>((s - 1) * B));
 #pragma unroll
             for (int j = 0; j < B; ++j) x[j] = h[j];
-            x[B] = g.P()[W::SPILL_TOP + s - 1];
+            x[B] = g.P()[W::SPILL_TOP + top_index<G, PAT>(s - 1)];
             x[B + 1] = 0u;
         }
         add_cc(x[0], lo[0]);
@@ -404,6 +449,9 @@ MPG_DI void cv_resolve_T(const Grp<typename W::LS> &g, uint32_t &c_add, uint32_t
     g.template bits<2>(pr, mk);
     c_add = mk[0] ? 1u : 0u;
     low_zero = mk[1] ? 0u : 1u;
+    // ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W); word NP-1 is the last word of
+    // slot G-1
+    if (g.t == G - 1) g.sm[W::OFF_L] = ~fin[0][M - 1] + low_zero;
     sts<M>(g.T() + pad32<W::PAD>(g.t * M), fin[0]);
     sts<M>(g.T() + pad32<W::PAD>((G + g.t) * M), fin[1]);
 }
@@ -460,9 +508,14 @@ MPG_DI void cv_cond_sub(const Grp<typename W::LS> &g, uint32_t (&c)[2][K], uint3
 // resolved words (skipped when lazy); result in X
 template <class W>
 MPG_DI void cv_resolve_hi(const Grp<typename W::LS> &g, uint32_t c_add, uint32_t low_zero, bool lazy) {
-    constexpr int H = W::H, G = W::G, NP = W::NP;
+    constexpr int H = W::H, G = W::G;
     uint32_t Z[H + 3];
-    lds<H + 3>(Z, g.T() + g.t * (H + 3));
+    {
+        uint32_t Zs[W::ZW];
+        lds<W::ZW>(Zs, g.T() + pad32<W::PAD>(g.t * W::ZW));
+#pragma unroll
+        for (int k = 0; k < H + 3; ++k) Z[k] = Zs[k];
+    }
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {   // sum over the instance's G lanes
         uint32_t o[H + 3];
@@ -470,8 +523,8 @@ MPG_DI void cv_resolve_hi(const Grp<typename W::LS> &g, uint32_t c_add, uint32_t
         for (int k = 0; k < H + 3; ++k) o[k] = __shfl_xor_sync(0xffffffffu, Z[k], off);
         add_n<H + 3>(Z, o);
     }
-    // L = ((-T) mod R)[NP-1] = ~T[NP-1] + [T[0 .. NP-1) == 0]  (mod W)
-    const uint32_t L = ~g.T()[pad32<W::PAD>(NP - 1)] + low_zero;
+    (void)low_zero;
+    const uint32_t L = g.sm[W::OFF_L];   // ((-T) mod R)[NP-1], saved by cv_resolve_T
     const uint32_t extra = (uint32_t)(((uint64_t)L - (uint64_t)Z[0]) >> 63);   // [L < Z[0]]
     uint32_t in0[H + 2], fin[2][H];
 #pragma unroll

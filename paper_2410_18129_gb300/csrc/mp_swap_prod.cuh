@@ -142,6 +142,7 @@ MPG_DI void swk_z_slots(const Grp<typename W::PS> &g, const uint32_t *SA, const 
     const int t = g.t;
     const bool even = (t & 1) == 0;
     Acc3<M> a;
+    uint32_t top[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int s = k ? G + t : t;
@@ -209,8 +210,9 @@ MPG_DI void swk_z_slots(const Grp<typename W::PS> &g, const uint32_t *SA, const 
             for (int j = M + 2; j < 2 * M + 1; ++j) addc_cc(V[j], 0u);
             addc(V[2 * M + 1], 0u);
         }
-        store_slot<M>(V, T + pad32<W::PAD>(s * M), swp_spill<W, M>(g, s));
+        top[k] = store_lohi<M>(V, T + pad32<W::PAD>(s * M), swp_hi<W, M>(g, s));
     }
+    store_tops<W>(g, top[0], top[1]);
 }
 
 template <class W>
