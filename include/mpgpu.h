@@ -255,6 +255,21 @@ int mp_tune_get_mont_karatsuba(uint32_t bits, uint32_t *karatsuba_from_bits);
  * without a kernel.
  */
 int mp_shape_residency(uint32_t bits, int G, int M, mp_red red, mp_algo algo, int *instances_per_sm);
+/*
+ * Window-table placement of modexp_consttime (Alg. 7's precomputed powers) for the class of
+ * `bits`: MP_TABLE_GLOBAL (the default) keeps each instance's 2^w entries in the caller's
+ * workspace and scans them from L2/HBM; MP_TABLE_SHARED keeps them in shared memory beside the
+ * instance's record, for the truncated reduction on the role-swapped kernels, at windows whose
+ * tables fit one block of 32 instances in an SM's shared memory (other calls keep the global
+ * placement; the workspace argument stays required either way). A shared table costs occupancy:
+ * 2^w x NP words per instance. mp_table_residency gives the instances per SM of that kernel at
+ * window w on the current device (0: the tables do not fit), for the class's selected shape;
+ * MP_ERR_UNIMPLEMENTED when that shape has no such kernel.
+ */
+typedef enum { MP_TABLE_GLOBAL = 0, MP_TABLE_SHARED = 1 } mp_table_placement;
+int mp_tune_set_table(uint32_t bits, mp_table_placement placement);
+int mp_tune_get_table(uint32_t bits, mp_table_placement *placement);
+int mp_table_residency(uint32_t bits, uint32_t window, int *instances_per_sm);
 
 /*
  * modexp_consttime without any device allocation. The paper has no counterpart:

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmpgpu.so")
 LAYOUT_INSTANCE_MAJOR, LAYOUT_INTERLEAVED = 0, 1
 ALGO_AUTO, ALGO_SCHOOLBOOK, ALGO_KARATSUBA, ALGO_KARATSUBA2 = 0, 1, 2, 3
 RED_TRUNCATED, RED_FULL, RED_CIOS = 0, 1, 2
+TABLE_GLOBAL, TABLE_SHARED = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libmpgpu.so is not built ({LIB_PATH}); run __graft_entry__.build() "
@@ -54,6 +55,9 @@ _SIG = {
     "mp_tune_set_mont_karatsuba": ([_u32, _u32], _i),
     "mp_tune_get_mont_karatsuba": ([_u32, ctypes.POINTER(_u32)], _i),
     "mp_shape_residency": ([_u32, _i, _i, _i, _i, ctypes.POINTER(_i)], _i),
+    "mp_tune_set_table": ([_u32, _i], _i),
+    "mp_tune_get_table": ([_u32, ctypes.POINTER(_i)], _i),
+    "mp_table_residency": ([_u32, _u32, ctypes.POINTER(_i)], _i),
     "modexp_mixed_workspace_bytes": ([_vp, _i], _sz),
     "modexp_consttime_mixed": ([_vp, _i, _i, _vp, _sz, _vp], _i),
     "modexp_table_bytes": ([_vp, _u32], _sz),
@@ -280,6 +284,25 @@ def tune_get_mont_karatsuba(bits: int) -> int:
     k = ctypes.c_uint32()
     _check(_lib.mp_tune_get_mont_karatsuba(bits, ctypes.byref(k)), "mp_tune_get_mont_karatsuba")
     return k.value
+
+
+def tune_set_table(bits: int, placement: int):
+    """Window-table placement of modexp_consttime for the class of `bits` (TABLE_GLOBAL or
+    TABLE_SHARED; see mp_tune_set_table)."""
+    _check(_lib.mp_tune_set_table(bits, placement), "mp_tune_set_table")
+
+
+def tune_get_table(bits: int) -> int:
+    p = _i()
+    _check(_lib.mp_tune_get_table(bits, ctypes.byref(p)), "mp_tune_get_table")
+    return p.value
+
+
+def table_residency(bits: int, window: int) -> int:
+    """Instances per SM of the exponentiation with shared-memory window tables (0: they do not fit)."""
+    r = _i()
+    _check(_lib.mp_table_residency(bits, window, ctypes.byref(r)), "mp_table_residency")
+    return r.value
 
 
 def shape_residency(bits: int, G: int = 0, M: int = 0, red: int = RED_TRUNCATED, algo: int = ALGO_AUTO) -> int:

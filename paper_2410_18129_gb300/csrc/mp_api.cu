@@ -58,6 +58,7 @@ struct SizeClass {
     ShapeOps tk;         // Montgomery products in the truncated Karatsuba form (mont/modexp null if absent)
     uint32_t mont_kara_from;   // AUTO Montgomery products and exponentiations of the truncated reduction use
                                // the Karatsuba form from this many bits (0: never)
+    int table_shared;          // modexp_consttime keeps the window tables in shared memory where they fit
 };
 static SizeClass g_classes[7];
 static std::once_flag g_classes_once;
@@ -510,6 +511,31 @@ extern "C" int mp_tune_get_mont_karatsuba(uint32_t bits, uint32_t *karatsuba_fro
     return MP_OK;
 }
 
+extern "C" int mp_tune_set_table(uint32_t bits, mp_table_placement placement) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (placement != MP_TABLE_GLOBAL && placement != MP_TABLE_SHARED) return MP_ERR_ARG;
+    class_for(words_for(bits))->table_shared = placement == MP_TABLE_SHARED ? 1 : 0;
+    return MP_OK;
+}
+
+extern "C" int mp_tune_get_table(uint32_t bits, mp_table_placement *placement) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (!placement) return MP_ERR_ARG;
+    *placement = class_for(words_for(bits))->table_shared ? MP_TABLE_SHARED : MP_TABLE_GLOBAL;
+    return MP_OK;
+}
+
+extern "C" int mp_table_residency(uint32_t bits, uint32_t window, int *instances_per_sm) {
+    if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
+    if (!instances_per_sm || window == 0 || window > 6) return MP_ERR_ARG;
+    const ShapeOps *sh = shape_for(words_for(bits));
+    if (!sh || !sh->residency_tab) return MP_ERR_UNIMPLEMENTED;
+    const int r = sh->residency_tab((int)window);
+    if (r < 0) return MP_ERR_CUDA;
+    *instances_per_sm = r;
+    return MP_OK;
+}
+
 extern "C" int mp_shape_residency(uint32_t bits, int G, int M, mp_red red, mp_algo algo, int *instances_per_sm) {
     if (bits == 0 || bits > MAX_BITS) return MP_ERR_SIZE;
     if (!instances_per_sm || (red != MP_RED_TRUNCATED && red != MP_RED_FULL && red != MP_RED_CIOS)) return MP_ERR_ARG;
@@ -572,6 +598,7 @@ extern "C" int modexp_consttime(uint32_t *y, const uint32_t *base, const uint32_
     A.out = y; A.a = base; A.e = exp; A.table = reinterpret_cast<uint32_t *>(ws);
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
+    A.tab_shared = class_for(c->np)->table_shared;
     int rc = cuda_status(sh->modexp(A, st));
     if (own) {
         if (cudaFreeAsync(ws, st) != cudaSuccess && rc == MP_OK) rc = MP_ERR_CUDA;

@@ -93,6 +93,7 @@ struct KArgs {
     int mode;                // exponentiation: 0 build the table and run, 1 build only, 2 run on a resident table
     int lazy;                // exponentiation: 4N <= W^NP, products skip the final subtraction (results < 2N)
     unsigned long long *cycles;   // measurement only: per request, SM clock cycles of its exponentiation
+    int tab_shared;          // exponentiation, mode 0: the window tables in shared memory (table unused)
 };
 
 // instance of this thread within its block, and its thread index within the instance
@@ -365,6 +366,9 @@ struct ShapeOps {
     cudaError_t (*modexp)(const KArgs &, cudaStream_t);
     cudaError_t (*kara)(const KArgs &, cudaStream_t);   // one-level Karatsuba product, or null
     int (*residency)(int red);   // instances per SM of the exponentiation kernel for reduction red (< 0: error)
+    // instances per SM of the truncated exponentiation with its window tables in shared memory at
+    // window w (0: the tables do not fit; < 0: error), or null when the shape has no such kernel
+    int (*residency_tab)(int w);
 };
 
 // resident instances per SM of a kernel with tpb threads, smem bytes of dynamic shared memory and

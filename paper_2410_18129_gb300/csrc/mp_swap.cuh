@@ -625,7 +625,15 @@ __global__ void __launch_bounds__(W::TPB, (swap_blocks_per_sm<W>())) k_mont_swap
 
 // Constant-time exponentiation (Alg. 7) in the role-swapped mapping: the same schedule as
 // modexp_group, with table accesses and global loads in the product view.
-template <class W, int RED>
+// words between two instances' window tables in shared memory: 2^w entries of NP words, plus 4
+// so that 32 instances' 16-byte accesses at one offset fall on distinct banks (as the records)
+template <class W>
+__host__ __device__ constexpr int tab_stride(int w) { return (1 << w) * W::NP + 4; }
+
+template <class W>
+constexpr size_t tab_smem(int w) { return W::SMEM + (size_t)32 * tab_stride<W>(w) * 4; }
+
+template <class W, int RED, bool TAB = false>
 MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
     using PS = typename W::PS;
     constexpr int M = W::M;
@@ -640,10 +648,19 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
     const size_t kt = A.mode == 0 ? k : kc;
     const size_t tb = A.mode == 0 ? A.batch : A.cbatch;
     uint4 *tab = reinterpret_cast<uint4 *>(A.table);
+    // TAB: this instance's table in shared memory after the block's 32 records, entries of NP
+    // words, instances tab_stride(w) words apart
+    uint32_t *ts = nullptr;
+    if constexpr (TAB) ts = v.p.sm - (size_t)(threadIdx.x & 31) * W::WORDS + 32 * W::WORDS +
+                            (size_t)(threadIdx.x & 31) * tab_stride<W>(w);
 
     auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
         uint32_t x[M];
         lds<M>(x, src + g.t * M);
+        if constexpr (TAB) {
+            sts<M>(ts + e * W::NP + g.t * M, x);
+            return;
+        }
         if (!valid) return;
         if constexpr (M % 4 == 0) {
 #pragma unroll
@@ -658,7 +675,9 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
         }
     };
     auto fetch = [&](int e, uint32_t (&x)[M]) {     // table entry e -> this thread's M words
-        if constexpr (M % 4 == 0) {
+        if constexpr (TAB) {
+            lds<M>(x, ts + e * W::NP + g.t * M);
+        } else if constexpr (M % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c) {
                 uint4 q = make_uint4(0, 0, 0, 0);
@@ -751,13 +770,13 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
     gstore<M>(A.out, x, A.layout, k, valid, g.t * M, A.n, A.batch);
 }
 
-template <class W, int RED>
+template <class W, int RED, bool TAB = false>
 __global__ void __launch_bounds__(W::TPB, (swap_blocks_per_sm<W>())) k_modexp_swap(KArgs A) {
     extern __shared__ uint4 smem4[];
     const Views<W> v = swap_views<W>(reinterpret_cast<uint32_t *>(smem4));
     const size_t k = swap_instance();
     const long long t0 = clock64();
-    modexp_swap<W, RED>(v, A, k);
+    modexp_swap<W, RED, TAB>(v, A, k);
     if (A.cycles && v.p.t == 0 && k < A.batch) A.cycles[k] = (unsigned long long)(clock64() - t0);
 }
 
@@ -781,7 +800,39 @@ struct SwapImpl {
     }
     static cudaError_t modexp(const KArgs &A, cudaStream_t st) {
         if (A.red == 2) return Lane::modexp(A, st);
+        if (A.tab_shared && A.mode == 0 && A.red == 0 && tab_fits(A.window)) return launch_tab(A, st);
         return A.red ? launch_swap<W, 3>(k_modexp_swap<W, 1>, A, st) : launch_swap<W, 2>(k_modexp_swap<W, 0>, A, st);
+    }
+    // the truncated exponentiation with its tables in shared memory fits one block on an SM
+    static bool tab_fits(int w) {
+        int dev = 0, optin = 0;
+        if (w < 1 || w > 6 || cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return false;
+        return tab_smem<W>(w) <= (size_t)optin;
+    }
+    static cudaError_t launch_tab(const KArgs &A, cudaStream_t st) {
+        static std::atomic<unsigned long long> attr_done{0ull};
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = smem_attr_once(attr_done, k_modexp_swap<W, 0, true>, (size_t)optin);
+        if (e != cudaSuccess) return e;
+        const size_t blocks = (A.batch + 31) / 32;
+        k_modexp_swap<W, 0, true><<<(unsigned)blocks, W::TPB, tab_smem<W>(A.window), st>>>(A);
+        return cudaGetLastError();
+    }
+    static int residency_tab(int w) {
+        if (!tab_fits(w)) return 0;
+        int dev = 0, optin = 0, blocks = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncSetAttribute(k_modexp_swap<W, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_modexp_swap<W, 0, true>, W::TPB, tab_smem<W>(w)) !=
+                cudaSuccess)
+            return -1;
+        return blocks * 32;
     }
     static int residency(int red) {
         if (red == 2) return Lane::residency(2);
@@ -801,6 +852,7 @@ struct SwapImpl {
         o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
         o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
         o.residency = &SwapImpl<Swap<G, M>, Lane>::residency;                                \
+        o.residency_tab = &SwapImpl<Swap<G, M>, Lane>::residency_tab;                        \
         return o;                                                                            \
     }                                                                                        \
     }
@@ -814,6 +866,7 @@ struct SwapImpl {
         o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
         o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
         o.residency = &SwapImpl<Swap<G, M>, Lane>::residency;                                \
+        o.residency_tab = &SwapImpl<Swap<G, M>, Lane>::residency_tab;                        \
         return o;                                                                            \
     }                                                                                        \
     }

@@ -335,6 +335,7 @@ static cudaError_t launch_kara_swap(const KArgs &A, cudaStream_t st) {
         o.mont = &SwapImpl<Swap<G, M>, Lane>::mont;                                          \
         o.modexp = &SwapImpl<Swap<G, M>, Lane>::modexp;                                      \
         o.residency = &SwapImpl<Swap<G, M>, Lane>::residency;                                \
+        o.residency_tab = &SwapImpl<Swap<G, M>, Lane>::residency_tab;                        \
         return o;                                                                            \
     }                                                                                        \
     }

@@ -1,8 +1,9 @@
 """Autotuner: per operand size, pick the group shape (threads per instance G x words per
-thread M), the exponentiation window (4..6), whether the Montgomery products of the truncated
-reduction use the truncated Karatsuba form, and the schoolbook/Karatsuba choice for
-products, by timing the library's own kernels on this GPU, each on whole residency rounds of
-its own; apply the choice through mp_tune_set / mp_tune_set_mont_karatsuba and cache it as
+thread M), the exponentiation window (4..6), the window-table placement (global or shared
+memory), whether the Montgomery products of the truncated reduction use the truncated
+Karatsuba form, and the schoolbook/Karatsuba choice for products, by timing the library's own kernels on this GPU, each on whole residency rounds of
+its own; apply the choice through mp_tune_set / mp_tune_set_table / mp_tune_set_mont_karatsuba
+and cache it as
 JSON keyed by GPU name, SM count and size.
 
     import paper_2410_18129_gb300.tune as tune
@@ -108,6 +109,37 @@ def tune(sizes=(1024, 2048, 3072, 4096), windows=(4, 5, 6), rounds: int = 2, log
                     best = (rate, G, M, w)
         _, G, M, w = best
         mp.tune_set(bits, G, M, w)
+        # window tables in shared memory (chosen shape), at the windows where they fit
+        table = "global"
+        for wt in windows:
+            try:
+                r = mp.table_residency(bits, wt)
+            except mp.MpError:
+                r = 0
+            if r <= 0:
+                continue
+            B = rounds * sms * r
+            ctx = ctx_for(B) if B <= Bmax else None
+            if ctx is None:
+                continue
+            A_b, E_b = _prefix(A, Bmax, B, bits), _prefix(E, Bmax, B, bits)
+            Y_b = torch.zeros_like(A_b)
+            ws = torch.empty(mp.modexp_workspace_bytes(B, bits, wt) // 4, dtype=torch.int32, device="cuda")
+            mp.tune_set_table(bits, mp.TABLE_SHARED)
+            try:
+                ms = _time(lambda: mp.modexp_consttime(Y_b, A_b, E_b, bits, ctx, wt, workspace=ws))
+            finally:
+                mp.tune_set_table(bits, mp.TABLE_GLOBAL)
+            rate = B / (ms / 1e3)
+            timings[f"modexp_shared_table_w{wt}"] = rate
+            if log:
+                log(f"tune {bits}: shared-memory tables w={wt} batch={B} ({r}/SM): {rate:,.0f} modexp/s")
+            if rate > best[0]:
+                best = (rate, G, M, wt)
+                table = "shared"
+        w = best[3]
+        mp.tune_set(bits, G, M, w)
+        mp.tune_set_table(bits, mp.TABLE_SHARED if table == "shared" else mp.TABLE_GLOBAL)
         # Montgomery products in the truncated Karatsuba form (Sec. 5.1) against the best choice
         mont_kara = NEVER
         if per_sm_tk:
@@ -137,7 +169,7 @@ def tune(sizes=(1024, 2048, 3072, 4096), windows=(4, 5, 6), rounds: int = 2, log
                 prod[nm] = 0.0
         timings.update({f"mul_{k}": v for k, v in prod.items()})
         kara = prod["karatsuba"] > prod["schoolbook"]
-        out[str(bits)] = {"G": G, "M": M, "window": w, "karatsuba_from_bits": bits if kara else NEVER,
+        out[str(bits)] = {"G": G, "M": M, "window": w, "table": table, "karatsuba_from_bits": bits if kara else NEVER,
                           "mont_karatsuba_from_bits": mont_kara, "modexp_per_s": best[0],
                           "residency_per_sm": {f"G{g}_M{m}": r for (g, m), r in per_sm.items()}, "timings": timings}
         for c in ctxs.values():
@@ -156,6 +188,7 @@ def _prefix(X: torch.Tensor, batch: int, B: int, bits: int) -> torch.Tensor:
 def apply(choice: dict):
     for bits, c in choice.items():
         mp.tune_set(int(bits), c["G"], c["M"], c["window"], c["karatsuba_from_bits"])
+        mp.tune_set_table(int(bits), mp.TABLE_SHARED if c.get("table") == "shared" else mp.TABLE_GLOBAL)
         k = c.get("mont_karatsuba_from_bits", NEVER)
         mp.tune_set_mont_karatsuba(int(bits), 0 if k == NEVER else k)
 

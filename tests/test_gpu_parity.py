@@ -418,6 +418,59 @@ def test_truncated_karatsuba_modexp(mp, bits, batch, window, layout):
     ctx.free()
 
 
+@pytest.mark.parametrize("bits,windows", [(1000, (2, 4, 5)), (1024, (1, 4, 5)), (2048, (2, 3, 4)),
+                                          (3072, (2, 3)), (4096, (1, 2))])
+def test_modexp_shared_tables(mp, bits, windows):
+    """Window tables in shared memory (mp_tune_set_table): equal to the oracle at every window
+    whose tables fit, on the extremes and a ragged batch; at w = 6, where they do not fit, the
+    call keeps the global tables and stays exact; the classical reduction keeps global tables."""
+    batch = 45 if bits > 3000 else 77
+    b = _tkara_batch(bits, batch, 8700 + bits)
+    ctx = mp.MontCtx(dev(mp, b.N, IL), batch, bits, IL)
+    want = oracle.modexp(b.a, b.e, b.ebits, b.N)
+    A, E = dev(mp, b.a, IL), dev(mp, b.e, IL)
+    Y = out_tensor(mp, batch, b.n, IL)
+    assert mp.tune_get_table(bits) == mp.TABLE_GLOBAL
+    try:
+        mp.tune_set_table(bits, mp.TABLE_SHARED)
+        assert mp.tune_get_table(bits) == mp.TABLE_SHARED
+        for w in windows:
+            assert mp.table_residency(bits, w) >= 32
+            Y.zero_()
+            mp.modexp_consttime(Y, A, E, b.ebits, ctx, w, mp.RED_TRUNCATED)
+            assert_equal(host(mp, Y, batch, b.n, IL), want, f"shared tables {bits} w={w}")
+        assert mp.table_residency(bits, 6) == 0
+        for w, red in ((6, mp.RED_TRUNCATED), (windows[0], mp.RED_FULL)):
+            Y.zero_()
+            mp.modexp_consttime(Y, A, E, b.ebits, ctx, w, red)
+            assert_equal(host(mp, Y, batch, b.n, IL), want, f"global fallback {bits} w={w} red={red}")
+    finally:
+        mp.tune_set_table(bits, mp.TABLE_GLOBAL)
+    ctx.free()
+
+
+@pytest.mark.parametrize("shape", [(16, 8), (8, 16)])
+def test_modexp_each_4096_bit_shape(mp, shape):
+    """Montgomery products and exponentiations on each role-swapped shape of the 4096-bit class,
+    both block-product reductions, against the oracle (extremes, ragged batch)."""
+    bits, batch = 4096, 37
+    b = _tkara_batch(bits, batch, 8800)
+    saved = mp.tune_get(bits)
+    try:
+        mp.tune_set(bits, *shape)
+        ctx = mp.MontCtx(dev(mp, b.N, IL), batch, bits, IL)
+        A, B, E = dev(mp, b.a, IL), dev(mp, b.b, IL), dev(mp, b.e, IL)
+        C = out_tensor(mp, batch, b.n, IL)
+        for red in (mp.RED_TRUNCATED, mp.RED_FULL):
+            mp.mont_mul(C, A, B, ctx, red)
+            assert_equal(host(mp, C, batch, b.n, IL), oracle.mont_def(b.a, b.b, b.N), f"mont_mul {shape} {red}")
+            mp.modexp_consttime(C, A, E, b.ebits, ctx, 5, red)
+            assert_equal(host(mp, C, batch, b.n, IL), oracle.modexp(b.a, b.e, b.ebits, b.N), f"modexp {shape} {red}")
+        ctx.free()
+    finally:
+        mp.tune_set(bits, saved["G"], saved["M"], saved["window"], saved["karatsuba_from_bits"])
+
+
 def test_truncated_karatsuba_unavailable(mp):
     """The Karatsuba form exists for the truncated reduction of the classes from 512 to 4096
     bits; the 256- and 4608-bit classes and the other reductions report MP_ERR_UNIMPLEMENTED

@@ -17,7 +17,7 @@ def test_tuner_small_run_and_apply():
     assert set(choice) == {"1024", "2048"}
     for bits, c in choice.items():
         assert (c["G"], c["M"]) in mp.shape_candidates(int(bits))
-        assert c["window"] in (4, 5) and c["modexp_per_s"] > 0
+        assert c["window"] in (4, 5) and c["modexp_per_s"] > 0 and c["table"] in ("global", "shared")
         assert all(r > 0 for r in c["residency_per_sm"].values())
     tune.apply(choice)
     for bits in (1024, 2048):
@@ -34,6 +34,7 @@ def test_tuner_small_run_and_apply():
         assert (got == oracle.modexp(b.a, b.e, 200, b.N)).all()
     for b, t in before.items():
         mp.tune_set(b, t["G"], t["M"], 0, 0)
+        mp.tune_set_table(b, mp.TABLE_GLOBAL)
 
 
 def test_residency_and_montgomery_karatsuba_switch():
