@@ -39,9 +39,9 @@ static constexpr uint32_t MAX_BITS = 32 * MAX_NP;
 // MP_ALGO_AUTO switch-over for products: measured on GB300, schoolbook wins at every size
 // (M products/s at a batch of 65536, schoolbook vs one Karatsuba level; role-swapped kernels:
 // 1024 bits mul 3826 / 3035, sqr 4980 / 3454; 2048 bits 1429 / 1218, 1932 / 1504; 3072 bits
-// 762 / 661, 1175 / 907; 4096 bits 470 / 464, 671 / 662; lane-mapped: 4108 bits 221 / 218,
-// 348 / 285; 4154 bits 239 / 220, 355 / 288), so AUTO never picks Karatsuba unless mp_tune_set
-// sets a switch-over
+// 762 / 661, 1175 / 907; 4096 bits 470 / 464, 671 / 662; 4108 and 4154 bits, lane-mapped
+// schoolbook and role-swapped Karatsuba: 305 / 300, 458 / 448), so AUTO never picks Karatsuba
+// unless mp_tune_set sets a switch-over
 static constexpr uint32_t KARATSUBA_FROM_BITS = 0xffffffffu;
 
 // Size classes: one per padded size NP. Each class has one or more compiled group
