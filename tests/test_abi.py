@@ -78,3 +78,32 @@ def test_noalloc_scratch_size_matches_the_header(lib_path):
     m = re.search(r"#define\s+MPGPU_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", open(HEADER).read())
     assert m, "header constant not found"
     assert lib.mp_noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))
+
+
+def test_tuning_calls_are_host_side(lib_path):
+    """The tuning setters and getters only touch the library's size-class table: their checks
+    and round trips need no GPU (values are restored afterwards)."""
+    lib = ctypes.CDLL(lib_path)
+    u32, i = ctypes.c_uint32, ctypes.c_int
+    lib.mp_tune_set_table.argtypes = [u32, i]
+    lib.mp_tune_get_table.argtypes = [u32, ctypes.POINTER(i)]
+    lib.mp_table_residency.argtypes = [u32, u32, ctypes.POINTER(i)]
+    lib.mp_tune_set_mont_karatsuba.argtypes = [u32, u32]
+    lib.mp_tune_get_mont_karatsuba.argtypes = [u32, ctypes.POINTER(u32)]
+    p = i(-1)
+    assert lib.mp_tune_get_table(2048, ctypes.byref(p)) == 0 and p.value == 0     # global by default
+    assert lib.mp_tune_set_table(2048, 1) == 0
+    assert lib.mp_tune_get_table(2000, ctypes.byref(p)) == 0 and p.value == 1     # the same size class
+    assert lib.mp_tune_get_table(1024, ctypes.byref(p)) == 0 and p.value == 0     # another class
+    assert lib.mp_tune_set_table(2048, 0) == 0
+    assert lib.mp_tune_set_table(2048, 2) == -1                                  # no such placement
+    assert lib.mp_tune_set_table(0, 0) == -2 and lib.mp_tune_set_table(1 << 20, 0) == -2
+    assert lib.mp_tune_get_table(2048, None) == -1
+    assert lib.mp_table_residency(2048, 0, ctypes.byref(p)) == -1                # window 0
+    assert lib.mp_table_residency(2048, 7, ctypes.byref(p)) == -1                # window above 6
+    assert lib.mp_table_residency(2048, 5, None) == -1
+    k = u32(1)
+    assert lib.mp_tune_get_mont_karatsuba(3072, ctypes.byref(k)) == 0 and k.value == 0
+    assert lib.mp_tune_set_mont_karatsuba(3072, 3000) == 0
+    assert lib.mp_tune_get_mont_karatsuba(3072, ctypes.byref(k)) == 0 and k.value == 3000
+    assert lib.mp_tune_set_mont_karatsuba(3072, 0) == 0
