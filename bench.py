@@ -734,7 +734,7 @@ def run_serving(rates=(1e4, 1e5, 1e6), seconds: float = 10.0, min_requests: int 
             w = pool.classes[bb]["window"]
             imad += modexp_imad(bb, bb, w, "trunc") if v else fixed_base_imad(bb, bb, w)
         adm = sv.AdmissionController(free_fn=free_fn, fraction=0.5, reserve=1 << 30, refresh=0.1)
-        cont = sv.serve(tr, sv.ContinuousExecutor(pool, tr, slots=4), slots=4, max_batch=16384, admission=adm)
+        cont = sv.serve(tr, sv.ContinuousExecutor(pool, tr, slots=2), slots=2, max_batch=16384, admission=adm)
         cs = cont.summary()
         span = float(np.nanmax(cont.done_at))
         cs["roofline"] = {"achieved": imad / span / 1e12, "frac": imad / span / 1e12 / peak if peak else None,
@@ -758,7 +758,9 @@ def run_serving(rates=(1e4, 1e5, 1e6), seconds: float = 10.0, min_requests: int 
         "workload": "serving: pool of 4096 moduli (1639 x 2048, 1024 x 1024, 819 x 3072, 614 x 4096 bits), fixed "
                     "base per modulus with resident tables, full-length exponents, Poisson arrivals, "
                     f">= {seconds:.0f} s or >= {min_requests} requests per rate",
-        "windows": {b: c["window"] for b, c in choice.items()}, "slots": 4, "max_batch": 16384,
+        "windows": {b: c["window"] for b, c in choice.items()}, "slots": 2,
+        "lanes": "one queue per size class, 2 batches in flight per class (a batch holds one class)",
+        "max_batch": 16384,
         "rates": out, "variable_base_rates": out_var,
         "variable_base": "every request brings its own base: its window table (2^w - 2 more products) is built "
                          "per request", "clocks": clk.summary(),

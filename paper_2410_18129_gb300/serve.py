@@ -8,13 +8,13 @@ over time; the loop
 
   * admits a batch only while the device bytes of the batches in flight fit a budget
     derived from the free device memory (AdmissionController, re-read as the run goes);
-  * keeps several batches in flight and forms the next batch from whatever is queued the
-    moment a slot frees up (continuous batching), so requests that arrive while others run
-    join the very next launch and the work of consecutive batches overlaps on the GPU;
-  * runs each size class of a batch on its own stream (one call of the library's mixed
-    entry point: the class's fixed-base and variable-base requests), with its result copy
-    and an event, so a request completes with its own class, not with the slowest class
-    of its batch;
+  * keeps one queue per size class and a few batches of each class in flight, and forms the
+    next batch of a class from whatever is queued the moment one of its slots frees up
+    (continuous batching), so requests that arrive while others run join the very next
+    launch of their class, the work of consecutive batches overlaps on the GPU, and a short
+    class never waits behind a long one;
+  * runs each batch on its slot's stream (one call of the library's mixed entry point: the
+    class's fixed-base and variable-base requests), with its result copy and an event;
   * drops requests that waited in the queue longer than a timeout (if one is given);
   * records per-request latency (arrival -> result on the host).
 
@@ -78,6 +78,7 @@ class Handle:
     reqs: np.ndarray
     nbytes: int
     token: object = None
+    lane: int = 0        # serve()'s lane index of the batch
 
 
 @dataclass
@@ -110,10 +111,20 @@ def serve(trace, executor, slots: int = 4, max_batch: int = 8192, admission: Adm
     order, up to max_batch and to what the admission controller allows. Requests still
     queued `timeout` seconds after their arrival are dropped. An executor with a
     completed(handle) method reports the requests of a batch as their results land (each
-    call returns those done since the previous one); otherwise a batch completes at once."""
+    call returns those done since the previous one); otherwise a batch completes at once.
+    An executor with `lanes` and lane_of(requests) (the continuous executor: one lane per
+    size class) gets one queue per lane and `slots` batches in flight per lane: a batch holds
+    one lane's requests, so a class waits only for its own batches; the lane whose oldest
+    request arrived first is served first."""
     count = len(trace.arrival)
     done_at = np.full(count, np.nan)
-    queue = collections.deque()
+    lanes = list(getattr(executor, "lanes", None) or [None])
+    lane_of = (executor.lane_of(np.arange(count)) if lanes[0] is not None
+               else np.zeros(count, dtype=np.int64))
+    key = {ln: i for i, ln in enumerate(lanes)}
+    lane_idx = np.array([key[x] for x in lane_of.tolist()], dtype=np.int64) if lanes[0] is not None else lane_of
+    queues = [collections.deque() for _ in lanes]
+    busy = [0] * len(lanes)
     inflight: list[Handle] = []
     nxt = 0
     completed = 0
@@ -126,13 +137,14 @@ def serve(trace, executor, slots: int = 4, max_batch: int = 8192, admission: Adm
         progressed = False
         now = clock() - t0
         while nxt < count and trace.arrival[nxt] <= now:
-            queue.append(nxt)
+            queues[lane_idx[nxt]].append(nxt)
             nxt += 1
         if timeout is not None:
-            while queue and now - trace.arrival[queue[0]] > timeout:   # FIFO: the oldest first
-                queue.popleft()
-                timed_out += 1
-                progressed = True
+            for queue in queues:
+                while queue and now - trace.arrival[queue[0]] > timeout:   # FIFO: the oldest first
+                    queue.popleft()
+                    timed_out += 1
+                    progressed = True
         for h in list(inflight):
             if partial:
                 for part in executor.completed(h):
@@ -146,27 +158,34 @@ def serve(trace, executor, slots: int = 4, max_batch: int = 8192, admission: Adm
                     admission.release(h.nbytes)
                 executor.finish(h)
                 inflight.remove(h)
+                busy[h.lane] -= 1
                 progressed = True
-        while queue and len(inflight) < slots:
-            take = min(len(queue), max_batch)
-            reqs = np.fromiter((queue[i] for i in range(take)), dtype=np.int64, count=take)
-            nbytes = executor.bytes_for(reqs)
-            if admission is not None:
-                while reqs.size and not admission.admit(nbytes):
-                    reqs = reqs[: reqs.size // 2]
-                    nbytes = executor.bytes_for(reqs) if reqs.size else 0
-                if not reqs.size:
-                    if not inflight:
-                        raise RuntimeError("one request needs more device memory than the admission budget")
-                    break
-            for _ in range(reqs.size):
-                queue.popleft()
-            inflight.append(executor.submit(reqs, nbytes))
-            batches += 1
-            max_seen = max(max_seen, int(reqs.size))
-            progressed = True
+        order = sorted((trace.arrival[q[0]], i) for i, q in enumerate(queues) if q)
+        for _, li in order:
+            queue = queues[li]
+            while queue and busy[li] < slots:
+                take = min(len(queue), max_batch)
+                reqs = np.fromiter((queue[i] for i in range(take)), dtype=np.int64, count=take)
+                nbytes = executor.bytes_for(reqs)
+                if admission is not None:
+                    while reqs.size and not admission.admit(nbytes):
+                        reqs = reqs[: reqs.size // 2]
+                        nbytes = executor.bytes_for(reqs) if reqs.size else 0
+                    if not reqs.size:
+                        if not inflight:
+                            raise RuntimeError("one request needs more device memory than the admission budget")
+                        break
+                for _ in range(reqs.size):
+                    queue.popleft()
+                h = executor.submit(reqs, nbytes) if lanes[0] is None else executor.submit(reqs, nbytes, lanes[li])
+                h.lane = li
+                inflight.append(h)
+                busy[li] += 1
+                batches += 1
+                max_seen = max(max_seen, int(reqs.size))
+                progressed = True
         if not progressed:
-            if nxt >= count and not inflight and not queue:
+            if nxt >= count and not inflight and not any(queues):
                 break
             idle()
     return ServeResult(done_at - trace.arrival, done_at, batches, max_seen,
@@ -282,20 +301,30 @@ class _GpuExecutorBase:
 
 
 class ContinuousExecutor(_GpuExecutorBase):
-    """Each batch takes one of `slots` slots; each size class of the batch runs on that slot's
-    stream for the class: async input copies, one call of the mixed entry point (the class's
-    fixed-base and variable-base requests), async result copies and an event. completed()
-    reports a class's requests as soon as its event has fired."""
+    """One lane per size class (serve() keeps a queue and `slots` batches in flight per lane);
+    a batch takes one of its class's slots and runs on that slot's stream: async input copies,
+    one call of the mixed entry point (the class's fixed-base and variable-base requests),
+    async result copies and an event. per_class=False: one set of `slots` slots shared by all
+    classes, a batch holding every class (each on its slot's stream for the class); completed()
+    then reports a class's requests as soon as its event has fired."""
 
-    def __init__(self, pool, trace, slots: int = 4, keep_results: bool = False):
+    def __init__(self, pool, trace, slots: int = 2, keep_results: bool = False, per_class: bool = True):
         super().__init__(pool, trace, keep_results)
         torch = self.torch
         self.streams = {(s, b): torch.cuda.Stream() for s in range(slots) for b in pool.classes}
-        self.free_slots = list(range(slots))
+        if per_class:
+            self.lanes = list(pool.classes)
+            self.free_slots = {b: list(range(slots)) for b in pool.classes}
+        else:
+            self.lanes = None
+            self.free_slots = {None: list(range(slots))}
 
-    def submit(self, reqs, nbytes):
+    def lane_of(self, reqs):
+        return self.bits_of[reqs]
+
+    def submit(self, reqs, nbytes, lane=None):
         torch, mp = self.torch, self.mp
-        slot = self.free_slots.pop()
+        slot = self.free_slots[lane].pop()
         parts = []
         for bits in self.pool.classes:
             sel = reqs[self.bits_of[reqs] == bits]
@@ -313,7 +342,7 @@ class ContinuousExecutor(_GpuExecutorBase):
                 ev.record(st)
             parts.append({"event": ev, "reqs": np.concatenate([p for p, _ in outs]), "keep": keep,
                           "host_out": host_out, "done": False})
-        return Handle(reqs, nbytes, {"slot": slot, "parts": parts})
+        return Handle(reqs, nbytes, {"slot": slot, "lane": lane, "parts": parts})
 
     def completed(self, h):
         out = []
@@ -329,7 +358,7 @@ class ContinuousExecutor(_GpuExecutorBase):
         return all(p["done"] for p in h.token["parts"])
 
     def finish(self, h):
-        self.free_slots.append(h.token["slot"])
+        self.free_slots[h.token["lane"]].append(h.token["slot"])
 
 
 class PlainExecutor(_GpuExecutorBase):

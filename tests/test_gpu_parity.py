@@ -41,7 +41,7 @@ def assert_equal(got, want, what):
     assert bad.size == 0, f"{what}: {bad.size} instances differ, first {bad[:8]}"
 
 
-SIZES = [64, 100, 256, 512, 1000, 1024, 2048, 3072, 4096, 4108, 4154]
+SIZES = [64, 100, 256, 512, 1000, 1024, 1500, 2048, 2500, 3072, 3500, 4000, 4096, 4108, 4154]
 
 
 # ------------------------------------------------------------------ products
@@ -291,7 +291,7 @@ def test_convert_round_trip(mp, w):
 
 # ------------------------------------------------------------------ one-level Karatsuba
 
-@pytest.mark.parametrize("bits", [520, 1000, 1024, 2048, 2078, 3072, 4096, 4108, 4154])
+@pytest.mark.parametrize("bits", [520, 1000, 1024, 1500, 2048, 2078, 2500, 3072, 3500, 4000, 4096, 4108, 4154])
 @pytest.mark.parametrize("layout", [IM, IL])
 def test_karatsuba_mul_sqr(mp, bits, layout):
     batch = 45 if bits > 3000 else 173

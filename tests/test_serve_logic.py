@@ -215,3 +215,50 @@ def test_variable_base_trace():
         b = tv.bases[k]
         assert b.shape == N.shape and int("".join(f"{w:08x}" for w in b[::-1]), 16) < \
             int("".join(f"{w:08x}" for w in N[::-1]), 16)
+
+
+class LaneExecutor(FakeExecutor):
+    """Requests with index divisible by 4 are 'slow' (a batch holding one takes 0.2 s of fake
+    time), the others 'fast' (0.01 s). With lanes, serve() keeps one queue per kind."""
+
+    def __init__(self, clock, lanes=True):
+        super().__init__(clock)
+        self.lanes = ["fast", "slow"] if lanes else None
+        self.busy = {"fast": 0, "slow": 0, None: 0}
+        self.max_busy = dict(self.busy)
+
+    def lane_of(self, reqs):
+        return np.where(np.asarray(reqs) % 4 == 0, "slow", "fast")
+
+    def submit(self, reqs, nbytes, lane=None):
+        h = super().submit(reqs, nbytes)
+        slow = bool((reqs % 4 == 0).any())
+        h.token = {"end": self.clock() + (0.2 if slow else 0.01), "lane": lane}
+        self.busy[lane] += 1
+        self.max_busy[lane] = max(self.max_busy[lane], self.busy[lane])
+        return h
+
+    def finish(self, h):
+        super().finish(h)
+        self.busy[h.token["lane"]] -= 1
+
+
+def test_lanes_keep_a_fast_class_off_a_slow_one():
+    """With one lane per class a batch holds one class and each class has its own slots, so
+    the fast class is served within its own batch time while slow batches are in flight;
+    without lanes the same requests wait behind batches that hold a slow request."""
+    tr = trace(2e3, 400, seed=3)
+    fast = np.arange(400) % 4 != 0
+    clk = FakeClock()
+    ex = LaneExecutor(clk)
+    res = serve(tr, ex, slots=2, max_batch=64, clock=clk, idle=clk.advance)
+    assert np.isfinite(res.latency).all()
+    for _, b in ex.batches:
+        assert len(set(ex.lane_of(b).tolist())) == 1               # one class per batch
+    assert ex.max_busy["fast"] <= 2 and ex.max_busy["slow"] <= 2 and ex.max_busy["slow"] >= 1
+    assert np.percentile(res.latency[fast], 90) < 0.05
+    clk2 = FakeClock()
+    ex2 = LaneExecutor(clk2, lanes=False)
+    res2 = serve(tr, ex2, slots=2, max_batch=64, clock=clk2, idle=clk2.advance)
+    assert np.isfinite(res2.latency).all()
+    assert np.percentile(res2.latency[fast], 90) > 0.1
