@@ -478,7 +478,7 @@ def bench_4096(args):
                     (lambda: mp.mp_sqr(C, A, B, bits, IL, algo))
                 for _ in range(args.warmup):
                     f()
-                ms = timed(f, max(3, args.steps))
+                ms = timed(f, max(50, args.steps))   # a launch is tens of microseconds: time many
                 prod[f"{op}_{nm}_{bits}"] = B / (ms / 1e3)
                 # bit-exact spot check against the oracle
                 got = mp.deinterleave(mp.to_host(C), B, 2 * n)[:16]
