@@ -272,6 +272,22 @@ int mp_tune_get_table(uint32_t bits, mp_table_placement *placement);
 int mp_table_residency(uint32_t bits, uint32_t window, int *instances_per_sm);
 
 /*
+ * Debug builds only (the library compiled with -DMPG_DEBUG_BOUNDS, e.g. by
+ * build.build(debug=True) into paper_2410_18129_gb300/_build_debug/): the kernels check
+ * their shared-memory block accesses (inside the block's shared memory, 16-byte aligned
+ * for vector accesses), the instance and word offsets of their global loads and stores,
+ * and the window-table entries of the exponentiations. A failed check records its first
+ * occurrence (kind in bits 56-63: 1 shared memory, 2 alignment, 3 load, 4 store, 5 table,
+ * 6 self-test; the offending offset below) and skips the access; nothing traps.
+ * mp_debug_bounds synchronises the device and returns the first recorded violation in
+ * *first (0: none), clearing the record; mp_debug_bounds_selftest launches a kernel that
+ * records one self-test violation without making any access. Release builds return
+ * MP_ERR_UNIMPLEMENTED from both.
+ */
+int mp_debug_bounds(unsigned long long *first);
+int mp_debug_bounds_selftest(void *stream);
+
+/*
  * modexp_consttime without any device allocation. The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory on the
  * call path, e.g. a service that reserved its whole memory budget up front, code

@@ -17,7 +17,8 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libmpgpu.so")
+# MPGPU_LIB: another build of the library (e.g. the bounds-checking debug build)
+LIB_PATH = os.environ.get("MPGPU_LIB") or os.path.join(_HERE, "_build", "libmpgpu.so")
 
 LAYOUT_INSTANCE_MAJOR, LAYOUT_INTERLEAVED = 0, 1
 ALGO_AUTO, ALGO_SCHOOLBOOK, ALGO_KARATSUBA, ALGO_KARATSUBA2 = 0, 1, 2, 3
@@ -56,6 +57,8 @@ _SIG = {
     "mp_tune_get_mont_karatsuba": ([_u32, ctypes.POINTER(_u32)], _i),
     "mp_shape_residency": ([_u32, _i, _i, _i, _i, ctypes.POINTER(_i)], _i),
     "mp_tune_set_table": ([_u32, _i], _i),
+    "mp_debug_bounds": ([ctypes.POINTER(ctypes.c_ulonglong)], _i),
+    "mp_debug_bounds_selftest": ([_vp], _i),
     "mp_tune_get_table": ([_u32, ctypes.POINTER(_i)], _i),
     "mp_table_residency": ([_u32, _u32, ctypes.POINTER(_i)], _i),
     "modexp_mixed_workspace_bytes": ([_vp, _i], _sz),
@@ -284,6 +287,19 @@ def tune_get_mont_karatsuba(bits: int) -> int:
     k = ctypes.c_uint32()
     _check(_lib.mp_tune_get_mont_karatsuba(bits, ctypes.byref(k)), "mp_tune_get_mont_karatsuba")
     return k.value
+
+
+def debug_bounds() -> int:
+    """Debug builds: the first recorded bounds violation (0: none), then cleared; synchronises the
+    device. Release builds raise MpError (MP_ERR_UNIMPLEMENTED)."""
+    v = ctypes.c_ulonglong()
+    _check(_lib.mp_debug_bounds(ctypes.byref(v)), "mp_debug_bounds")
+    return v.value
+
+
+def debug_bounds_selftest():
+    """Debug builds: record one self-test violation (kind 6) without any memory access."""
+    _check(_lib.mp_debug_bounds_selftest(_stream()), "mp_debug_bounds_selftest")
 
 
 def tune_set_table(bits: int, placement: int):

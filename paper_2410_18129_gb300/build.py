@@ -1,7 +1,9 @@
 """Build libmpgpu.so (the C ABI of include/mpgpu.h) for sm_103a with nvcc.
 
 Each translation unit under csrc/ is compiled in parallel, then linked into
-paper_2410_18129_gb300/_build/libmpgpu.so (in-tree, git-ignored)."""
+paper_2410_18129_gb300/_build/libmpgpu.so (in-tree, git-ignored). build(debug=True) builds the
+bounds-checking variant (-DMPG_DEBUG_BOUNDS, see mp_debug_bounds in include/mpgpu.h) into
+paper_2410_18129_gb300/_build_debug/libmpgpu.so."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -16,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmpgpu.so")
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC,
          "--expt-relaxed-constexpr"]
@@ -36,8 +39,8 @@ def _deps() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INC, "*.h")))
 
 
-def _compile(src: str, verbose: bool, extra: list[str]) -> str:
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, extra: list[str], out: str = OUT) -> str:
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(d) for d in _deps()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
         return obj
@@ -53,22 +56,25 @@ def _compile(src: str, verbose: bool, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    extra = list(extra or []) + os.environ.get("MPG_EXTRA_FLAGS", "").split()
+def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None,
+          debug: bool = False) -> str:
+    out = OUT_DEBUG if debug else OUT
+    lib = os.path.join(out, "libmpgpu.so")
+    os.makedirs(out, exist_ok=True)
+    extra = list(extra or []) + os.environ.get("MPG_EXTRA_FLAGS", "").split() + (["-DMPG_DEBUG_BOUNDS"] if debug else [])
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, extra), srcs))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, extra, out), srcs))
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+        return lib
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

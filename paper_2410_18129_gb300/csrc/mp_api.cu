@@ -25,6 +25,7 @@ ShapeOps shape_ops_8_18();
 ShapeOps shape_ops_8_8_w();
 cudaError_t kara2_128(const KArgs &, cudaStream_t);
 cudaError_t kara2_144(const KArgs &, cudaStream_t);
+unsigned long long dbg_take_kara2();
 ShapeOps tkara_ops_16();
 ShapeOps tkara_ops_32();
 ShapeOps tkara_ops_64();
@@ -767,4 +768,47 @@ extern "C" int modexp_consttime_noalloc(uint32_t *y, const uint32_t *base, const
     A.ebits = (int)exp_bits; A.ne = exp_bits ? (int)((exp_bits + 31) / 32) : 1; A.window = (int)window;
     A.red = (int)red;
     return cuda_status(sh->modexp(A, S(stream)));
+}
+
+// ------------------------------------------------------------------ debug builds
+
+#ifdef MPG_DEBUG_BOUNDS
+// records one violation without making the access it describes (the checks' own test)
+__global__ void k_dbg_selftest() {
+    if (threadIdx.x == 0 && blockIdx.x == 0) dbg_ok(false, DBG_SELFTEST, 12345ull);
+}
+#endif
+
+extern "C" int mp_debug_bounds(unsigned long long *first) {
+#ifdef MPG_DEBUG_BOUNDS
+    if (!first) return MP_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return MP_ERR_CUDA;
+    init_classes();
+    unsigned long long v = 0;
+    auto take = [&](unsigned long long x) {
+        if (!v) v = x;
+    };
+    for (auto &c : g_classes) {
+        for (int i = 0; i < c.nshapes; ++i)
+            if (c.shapes[i].dbg) take(c.shapes[i].dbg());
+        if (c.tk.dbg) take(c.tk.dbg());
+    }
+    take(dbg_take_kara2());
+    take(dbg_take());   // this unit's own kernels (conversion, context set-up)
+    *first = v;
+    return MP_OK;
+#else
+    (void)first;
+    return MP_ERR_UNIMPLEMENTED;
+#endif
+}
+
+extern "C" int mp_debug_bounds_selftest(void *stream) {
+#ifdef MPG_DEBUG_BOUNDS
+    k_dbg_selftest<<<1, 32, 0, S(stream)>>>();
+    return cuda_status(cudaGetLastError());
+#else
+    (void)stream;
+    return MP_ERR_UNIMPLEMENTED;
+#endif
 }

@@ -144,6 +144,13 @@ MPG_DI void gsync() { __syncwarp(); }
 
 template <int K>
 MPG_DI void lds(uint32_t (&x)[K], const uint32_t *p) {
+#ifdef MPG_DEBUG_BOUNDS
+    if (!smem_ok(p, 4 * K, K % 4 == 0)) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) x[k] = 0u;
+        return;
+    }
+#endif
     if constexpr (K % 4 == 0) {
 #pragma unroll
         for (int k = 0; k < K / 4; ++k) {
@@ -164,6 +171,9 @@ MPG_DI void lds(uint32_t (&x)[K], const uint32_t *p) {
 
 template <int K>
 MPG_DI void sts(uint32_t *p, const uint32_t (&x)[K]) {
+#ifdef MPG_DEBUG_BOUNDS
+    if (!smem_ok(p, 4 * K, K % 4 == 0)) return;
+#endif
     if constexpr (K % 4 == 0) {
 #pragma unroll
         for (int k = 0; k < K / 4; ++k)

@@ -4,4 +4,9 @@
 namespace mpg {
 cudaError_t kara2_128(const KArgs &A, cudaStream_t st) { return launch_kara2<Shape<8, 4>, 128>(A, st); }
 cudaError_t kara2_144(const KArgs &A, cudaStream_t st) { return launch_kara2<Shape<4, 9>, 64>(A, st); }
+#ifdef MPG_DEBUG_BOUNDS
+unsigned long long dbg_take_kara2() { return dbg_take(); }
+#else
+unsigned long long dbg_take_kara2() { return 0; }
+#endif
 }  // namespace mpg

@@ -21,6 +21,9 @@ MPG_DI size_t widx(int layout, size_t k, int i, int words, size_t batch) {
 template <int M>
 MPG_DI void gload(uint32_t (&x)[M], const uint32_t *p, int layout, size_t k, bool valid, int w0,
                   int words, size_t batch) {
+#ifdef MPG_DEBUG_BOUNDS
+    if (valid && !dbg_ok(k < batch && w0 >= 0, DBG_LOAD, k)) valid = false;
+#endif
     if constexpr (M % 4 == 0) {
         if (layout == LAYOUT_IL && (w0 & 3) == 0) {
 #pragma unroll
@@ -46,6 +49,9 @@ MPG_DI void gload(uint32_t (&x)[M], const uint32_t *p, int layout, size_t k, boo
 template <int M>
 MPG_DI void gstore(uint32_t *p, const uint32_t (&x)[M], int layout, size_t k, bool valid, int w0, int words,
                    size_t batch) {
+#ifdef MPG_DEBUG_BOUNDS
+    if (valid && !dbg_ok(k < batch && w0 >= 0, DBG_STORE, k)) valid = false;
+#endif
     if (!valid) return;
     if constexpr (M % 4 == 0) {
         if (layout == LAYOUT_IL && (w0 & 3) == 0) {
@@ -244,6 +250,9 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
     auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
         uint32_t x[M];
         lds<M>(x, src + g.t * M);
+#ifdef MPG_DEBUG_BOUNDS
+        if (valid && !dbg_ok(e >= 0 && e < E && kt < tb, DBG_TABLE, (unsigned long long)e * tb + kt)) return;
+#endif
         if (!valid) return;
         if constexpr (M % 4 == 0) {
 #pragma unroll
@@ -259,6 +268,12 @@ MPG_DI void modexp_group(const Grp<S> &g, const KArgs &A, size_t k) {
         }
     };
     auto fetch = [&](int e, uint32_t (&x)[M]) {     // table entry e -> this thread's M words
+#ifdef MPG_DEBUG_BOUNDS
+        if (valid && !dbg_ok(e >= 0 && e < E && kt < tb, DBG_TABLE, (unsigned long long)e * tb + kt)) {
+            zero<M>(x);
+            return;
+        }
+#endif
         if constexpr (M % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < M / 4; ++c) {
@@ -369,6 +384,9 @@ struct ShapeOps {
     // instances per SM of the truncated exponentiation with its window tables in shared memory at
     // window w (0: the tables do not fit; < 0: error), or null when the shape has no such kernel
     int (*residency_tab)(int w);
+    // debug builds: takes (reads and clears) the first bounds violation recorded by the kernels of
+    // this shape's translation unit (0: none); null in release builds
+    unsigned long long (*dbg)();
 };
 
 // resident instances per SM of a kernel with tpb threads, smem bytes of dynamic shared memory and
@@ -443,7 +461,7 @@ struct ShapeImpl {
     static ShapeOps ops() {
         // the warp-mapped variant of a shape reports G < 0 (see mp_shape_candidates)
         return ShapeOps{S::WMAP ? -S::G : S::G, S::M, S::NP, TPB, (size_t)(TPB / S::G) * S::WORDS * 4, &mul, &mont,
-                        &modexp, nullptr, &residency};
+                        &modexp, nullptr, &residency, nullptr, MPG_DBG_TAKE};
     }
 };
 

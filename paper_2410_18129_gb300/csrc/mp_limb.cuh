@@ -6,6 +6,7 @@
 // Every function here runs the same instruction sequence for every input value.
 #pragma once
 #include <cstdint>
+#include "mp_debug.cuh"
 
 namespace mpg {
 

@@ -657,6 +657,9 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
     auto put = [&](int e, const uint32_t *src) {   // this thread's M words -> table entry e
         uint32_t x[M];
         lds<M>(x, src + g.t * M);
+#ifdef MPG_DEBUG_BOUNDS
+        if (valid && !dbg_ok(e >= 0 && e < E && kt < tb, DBG_TABLE, (unsigned long long)e * tb + kt)) return;
+#endif
         if constexpr (TAB) {
             sts<M>(ts + e * W::NP + g.t * M, x);
             return;
@@ -675,6 +678,12 @@ MPG_DI void modexp_swap(const Views<W> &v, const KArgs &A, size_t k) {
         }
     };
     auto fetch = [&](int e, uint32_t (&x)[M]) {     // table entry e -> this thread's M words
+#ifdef MPG_DEBUG_BOUNDS
+        if (valid && !dbg_ok(e >= 0 && e < E && kt < tb, DBG_TABLE, (unsigned long long)e * tb + kt)) {
+            zero<M>(x);
+            return;
+        }
+#endif
         if constexpr (TAB) {
             lds<M>(x, ts + e * W::NP + g.t * M);
         } else if constexpr (M % 4 == 0) {

@@ -258,7 +258,7 @@ struct TKaraImpl {
     }
     static ShapeOps ops() {
         return ShapeOps{KS::G, KS::M, KS::NP, TPB, (size_t)(TPB / KS::G) * KS::WORDS * 4, nullptr, &mont, &modexp,
-                        nullptr, &residency};
+                        nullptr, &residency, nullptr, MPG_DBG_TAKE};
     }
 };
 
