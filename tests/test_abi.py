@@ -107,3 +107,14 @@ def test_tuning_calls_are_host_side(lib_path):
     assert lib.mp_tune_set_mont_karatsuba(3072, 3000) == 0
     assert lib.mp_tune_get_mont_karatsuba(3072, ctypes.byref(k)) == 0 and k.value == 3000
     assert lib.mp_tune_set_mont_karatsuba(3072, 0) == 0
+
+
+def test_debug_build_compiles_and_exports(lib_path):
+    """The bounds-checking variant (-DMPG_DEBUG_BOUNDS) cross-compiles here too and exports the same
+    boundary, so its GPU test cannot fail on a build break alone."""
+    import __graft_entry__
+    dbg = __graft_entry__._load_build_script().build(debug=True)
+    assert dbg != lib_path and os.path.exists(dbg)
+    out = subprocess.run(["nm", "-D", "--defined-only", dbg], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, flags=re.M))
+    assert not [n for n in declared_functions() if n not in exported]
